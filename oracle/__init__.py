@@ -1,0 +1,186 @@
+"""FP64 CPU oracle (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg load this package.  The CUDA library never imports it, and it imports
+nothing from the CUDA library.  The arithmetic lives in ``brahms_oracle.c``
+(plain C99 complex double, own recursive FFT); this module compiles it with
+gcc and marshals numpy arrays.
+
+Parity status of each function (what pins it, see tests/test_oracle_*.py):
+  fft1d / fft3        naive O(N^2) DFT, numpy.fft, Parseval, impulse<->constant
+  linear_step         Gaussian-beam waist w(z) with focus at L/2 (diffraction
+                      sign), Gaussian-pulse broadening (GVD), exact integer
+                      shifts (walk-off and group-velocity mismatch), loss
+                      decay, composition and unitarity
+  nonlinear_step      plane-wave tanh^2 SHG, undepleted sinc SHG/SFG/DFG,
+                      undepleted-pump parametric gain (cosh/sinh)
+  propagate           energy and Manley-Rowe invariants, second-order
+                      self-convergence in dz
+  energy              analytic Gaussian-beam/pulse energy
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "brahms_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE FP64; no fast-math)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-fcx-fortran-rules",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm", "-lpthread"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Field(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("n", ctypes.c_double), ("delta", ctypes.c_double),
+                ("k2", ctypes.c_double), ("k3", ctypes.c_double), ("rho", ctypes.c_double),
+                ("alpha", ctypes.c_double)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nt", ctypes.c_int), ("nf", ctypes.c_int),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+                ("d_eff", ctypes.c_double), ("f", _Field * 3)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            dp = P(ctypes.c_double)
+            vp = ctypes.c_void_p
+            lib.orc_set_threads.argtypes = [ctypes.c_int]
+            lib.orc_get_threads.restype = ctypes.c_int
+            lib.orc_dft_naive.argtypes = [vp, vp, ctypes.c_int, ctypes.c_int]
+            lib.orc_fft1d.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            lib.orc_fft3.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.orc_angular_freq.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double]
+            lib.orc_angular_freq.restype = ctypes.c_double
+            lib.orc_linear_step.argtypes = [P(_Problem), vp, ctypes.c_double]
+            lib.orc_kappa.argtypes = [P(_Problem), ctypes.c_int]
+            lib.orc_kappa.restype = ctypes.c_double
+            lib.orc_nonlinear_step.argtypes = [P(_Problem), vp, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double]
+            lib.orc_rk4_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, vp]
+            lib.orc_propagate.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp]
+            lib.orc_propagate.restype = ctypes.c_int
+            lib.orc_energy.argtypes = [P(_Problem), vp, dp, dp]
+            _lib = lib
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
+
+
+def _c128(a: np.ndarray) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+def dft_naive(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    x = _c128(x)
+    out = np.empty_like(x)
+    _load().orc_dft_naive(x.ctypes.data, out.ctypes.data, x.size, sign)
+    return out
+
+
+def fft1d(x: np.ndarray, sign: int = -1) -> np.ndarray:
+    y = _c128(x).copy()
+    _load().orc_fft1d(y.ctypes.data, y.size, sign)
+    return y
+
+
+def fft3(a: np.ndarray, sign: int = -1) -> np.ndarray:
+    """Unnormalised 3D DFT of an [nt, ny, nx] array (sign -1 forward)."""
+    y = _c128(a).copy()
+    nt, ny, nx = y.shape
+    _load().orc_fft3(y.ctypes.data, nx, ny, nt, sign)
+    return y
+
+
+def angular_freq(m: int, n: int, d: float) -> float:
+    return float(_load().orc_angular_freq(m, n, d))
+
+
+def make_problem(grid, fields, d_eff: float) -> _Problem:
+    p = _Problem()
+    p.nx, p.ny, p.nt = grid.nx, grid.ny, grid.nt
+    p.nf = len(fields)
+    p.dx, p.dy, p.dt = grid.dx, grid.dy, grid.dt
+    p.d_eff = d_eff
+    for i, f in enumerate(fields):
+        p.f[i] = _Field(*f.as_tuple())
+    return p
+
+
+def _stack(fields: Sequence[np.ndarray]) -> np.ndarray:
+    return np.ascontiguousarray(np.stack([_c128(f) for f in fields]))
+
+
+def kappa(prob: _Problem, f: int) -> float:
+    return float(_load().orc_kappa(ctypes.byref(prob), f))
+
+
+def linear_step(prob: _Problem, fields: Sequence[np.ndarray], dz: float) -> np.ndarray:
+    a = _stack(fields)
+    _load().orc_linear_step(ctypes.byref(prob), a.ctypes.data, dz)
+    return a
+
+
+def nonlinear_step(prob: _Problem, fields: Sequence[np.ndarray], phi_a: float, dk: float,
+                   h: float) -> np.ndarray:
+    a = _stack(fields)
+    _load().orc_nonlinear_step(ctypes.byref(prob), a.ctypes.data, phi_a, dk, h)
+    return a
+
+
+def propagate(prob: _Problem, fields: Sequence[np.ndarray], nz: int, dz: float, dk,
+              phi0: float = 0.0, check: bool = True):
+    """Run nz split steps.  ``dk`` is a scalar or an array of nz per-step values.
+    Returns (fields[nf, nt, ny, nx] complex128, phi_end)."""
+    a = _stack(fields)
+    dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
+    phi = ctypes.c_double(phi0)
+    rc = _load().orc_propagate(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz),
+                               dks.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(phi))
+    if check and rc != 0:
+        raise FloatingPointError("oracle: non-finite fields (dz too large)")
+    return a, phi.value
+
+
+def energy(prob: _Problem, fields: Sequence[np.ndarray]):
+    a = _stack(fields)
+    e = np.zeros(prob.nf)
+    ph = np.zeros(prob.nf)
+    dp = ctypes.POINTER(ctypes.c_double)
+    _load().orc_energy(ctypes.byref(prob), a.ctypes.data, e.ctypes.data_as(dp), ph.ctypes.data_as(dp))
+    return e, ph
+
+
+def problem_from(p) -> _Problem:
+    """Oracle problem struct from a workloads.Problem."""
+    return make_problem(p.grid, p.fields, p.d_eff)

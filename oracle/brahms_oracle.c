@@ -1,0 +1,413 @@
+/*
+ * FP64 CPU oracle for the split-step Fourier solution of the coupled chi(2)
+ * three-wave-mixing equations in (3+1)D (x, y, tau propagated along z).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, plain, obviously correct
+ * statement of what the CUDA path computes.  Only the test suite, the smoke
+ * check and the benchmark's CPU-baseline leg may load it.  It shares no code,
+ * header, table or constant generator with the CUDA library.
+ *
+ * What it follows (paper sections and equations):
+ *   - coupled equations, Sec. 2, Eqs. CEp/CEs/CEi, with kappa = 2 pi d_eff/(n lambda)
+ *   - dispersion operator, Eq. dispOp; diffraction/walk-off operator, Eq. diffOp
+ *   - symmetric split step N(dz/2) L(dz) N(dz/2), Sec. 3.1, Eq. expon and the
+ *     field-evolution equation that follows it
+ *   - fourth-order Runge-Kutta for the nonlinear part, Sec. 3.1
+ *   - power / energy, Sec. 6, P = 1/2 c eps0 n  integral |A|^2 dx dy
+ *
+ * Readings where the paper is silent or inconsistent (each is also pinned by a
+ * test against a closed form):
+ *   R1  diffraction enters as +(i/2k)(d2/dx2 + d2/dy2), the sign that the
+ *       paper's own focused Gaussian beam (Eq. gaussianbeam) solves.
+ *   R2  third-order dispersion is the unitary -[... - (k'''/6) d3/dtau3].
+ *   R3  the scalar Eqs. CEp/CEs/CEi are used, not the garbled matrix form.
+ *   R4  two-field degenerate SHG: fields (SH, F), SH plays the pump and F both
+ *       signal and idler, with a 1/2 degeneracy factor on the SH equation:
+ *         dA_SH/dz = i (kappa_SH/2) A_F^2 e^{-i Phi},
+ *         dA_F /dz = i kappa_F A_SH A_F^*  e^{+i Phi}.
+ *   R5  the mismatch phase stays in the nonlinear terms, Phi(z) = int_0^z dk.
+ *   R6  the first RK4 half step spans [z_j, z_j + dz/2], the second
+ *       [z_j + dz/2, z_j + dz]; Phi is evaluated at each RK4 stage's z.
+ *   R7  forward DFT is unnormalised with e^{-2 pi i m n / N}; the inverse
+ *       carries 1/N; angular frequencies follow numpy's fftfreq (the Nyquist
+ *       bin is negative), so d/dx -> +i kx and d/dtau -> +i Omega.
+ *
+ * Data layout: fields[f][tau][y][x], x fastest, complex128.
+ */
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_C0 299792458.0
+#define ORC_EPS0 8.8541878128e-12
+#define ORC_HBAR 1.054571817e-34
+#define ORC_TWO_PI 6.283185307179586476925286766559
+
+typedef struct {
+  double lambda; /* vacuum wavelength [m] */
+  double n;      /* refractive index */
+  double delta;  /* 1/v_s - 1/v_lambda [s/m] */
+  double k2;     /* GVD [s^2/m] */
+  double k3;     /* TOD [s^3/m] */
+  double rho;    /* walk-off angle [rad] */
+  double alpha;  /* loss [1/m] */
+} orc_field;
+
+typedef struct {
+  int nx, ny, nt, nf;
+  double dx, dy, dt;
+  double d_eff;
+  orc_field f[3];
+} orc_problem;
+
+/* ------------------------------------------------------------------------ */
+/* Threads: a plain fork-join over an index range.                           */
+/* ------------------------------------------------------------------------ */
+static int g_threads = 1;
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return g_threads; }
+
+typedef void (*range_fn)(void* ctx, int64_t begin, int64_t end);
+typedef struct {
+  range_fn fn;
+  void* ctx;
+  int64_t begin, end;
+} range_job;
+
+static void* range_trampoline(void* p) {
+  range_job* j = (range_job*)p;
+  j->fn(j->ctx, j->begin, j->end);
+  return NULL;
+}
+
+static void parallel_for(int64_t count, range_fn fn, void* ctx) {
+  int nt = g_threads;
+  if (nt <= 1 || count < 2) {
+    fn(ctx, 0, count);
+    return;
+  }
+  if (nt > count) nt = (int)count;
+  pthread_t th[256];
+  range_job jobs[256];
+  if (nt > 256) nt = 256;
+  for (int i = 0; i < nt; ++i) {
+    jobs[i].fn = fn;
+    jobs[i].ctx = ctx;
+    jobs[i].begin = count * i / nt;
+    jobs[i].end = count * (i + 1) / nt;
+  }
+  for (int i = 1; i < nt; ++i) pthread_create(&th[i], NULL, range_trampoline, &jobs[i]);
+  range_trampoline(&jobs[0]);
+  for (int i = 1; i < nt; ++i) pthread_join(th[i], NULL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* DFT: the plain O(N^2) definition and a recursive mixed-radix FFT.          */
+/* ------------------------------------------------------------------------ */
+
+/* out[m] = sum_n in[n] exp(sign * 2 pi i m n / N), no normalisation. */
+void orc_dft_naive(const cplx* in, cplx* out, int n, int sign) {
+  for (int m = 0; m < n; ++m) {
+    cplx s = 0;
+    for (int k = 0; k < n; ++k) {
+      long long e = ((long long)m * k) % n;
+      double ang = sign * ORC_TWO_PI * (double)e / (double)n;
+      s += in[k] * (cos(ang) + I * sin(ang));
+    }
+    out[m] = s;
+  }
+}
+
+static int smallest_factor(int n) {
+  if (n % 2 == 0) return 2;
+  for (int p = 3; p * p <= n; p += 2)
+    if (n % p == 0) return p;
+  return n;
+}
+
+/* Decimation in time: y[0..n) = DFT_n of x[0], x[stride], ..., x[(n-1) stride].
+ * w[k] = exp(sign 2 pi i k / ntop) for the top-level length ntop; wstep = ntop/n.
+ * For radix R = smallest factor of n, with m = n/R, the R sub-transforms of the
+ * decimated sequences x[r + R q] land in y[r m .. r m + m), and are combined as
+ *   Y[k + m s] = sum_r  W_n^{r (k + m s)}  Y_r[k].                           */
+static void fft_rec(const cplx* x, long stride, cplx* y, int n, const cplx* w, int wstep,
+                    int ntop) {
+  if (n == 1) {
+    y[0] = x[0];
+    return;
+  }
+  int R = smallest_factor(n);
+  int m = n / R;
+  for (int r = 0; r < R; ++r) fft_rec(x + r * stride, stride * R, y + r * m, m, w, wstep * R, ntop);
+  cplx t[64];
+  cplx* tt = t;
+  cplx* heap = NULL;
+  if (R > 64) {
+    heap = (cplx*)malloc(sizeof(cplx) * R);
+    tt = heap;
+  }
+  for (int k = 0; k < m; ++k) {
+    for (int r = 0; r < R; ++r) tt[r] = y[r * m + k];
+    for (int s = 0; s < R; ++s) {
+      cplx acc = 0;
+      for (int r = 0; r < R; ++r) {
+        long long e = ((long long)r * (k + (long long)m * s)) % n; /* exponent of W_n */
+        acc += tt[r] * w[(e * wstep) % ntop];
+      }
+      y[k + m * s] = acc;
+    }
+  }
+  free(heap);
+}
+
+static cplx* twiddle_table(int n, int sign) {
+  cplx* w = (cplx*)malloc(sizeof(cplx) * n);
+  for (int k = 0; k < n; ++k) {
+    double ang = sign * ORC_TWO_PI * (double)k / (double)n;
+    w[k] = cos(ang) + I * sin(ang);
+  }
+  return w;
+}
+
+/* In place, unnormalised: x <- sum_n x[n] exp(sign 2 pi i m n / N). */
+void orc_fft1d(cplx* x, int n, int sign) {
+  cplx* w = twiddle_table(n, sign);
+  cplx* tmp = (cplx*)malloc(sizeof(cplx) * n);
+  memcpy(tmp, x, sizeof(cplx) * n);
+  fft_rec(tmp, 1, x, n, w, 1, n);
+  free(tmp);
+  free(w);
+}
+
+/* One axis of a 3D transform: pencils of length n at element stride `stride`. */
+typedef struct {
+  cplx* a;
+  int n;
+  long stride;
+  int inner;  /* number of consecutive pencils sharing an outer index */
+  long outer_stride;
+  const cplx* w;
+} axis_job;
+
+static void axis_range(void* p, int64_t b, int64_t e) {
+  axis_job* j = (axis_job*)p;
+  cplx* buf = (cplx*)malloc(sizeof(cplx) * j->n * 2);
+  cplx* out = buf + j->n;
+  for (int64_t pi = b; pi < e; ++pi) {
+    long o = (long)(pi / j->inner), i = (long)(pi % j->inner);
+    cplx* base = j->a + o * j->outer_stride + i;
+    for (int k = 0; k < j->n; ++k) buf[k] = base[k * j->stride];
+    fft_rec(buf, 1, out, j->n, j->w, 1, j->n);
+    for (int k = 0; k < j->n; ++k) base[k * j->stride] = out[k];
+  }
+  free(buf);
+}
+
+/* In-place unnormalised 3D DFT of one [nt][ny][nx] array. */
+void orc_fft3(cplx* a, int nx, int ny, int nt, int sign) {
+  axis_job j;
+  j.a = a;
+  /* x: pencils contiguous */
+  cplx* wx = twiddle_table(nx, sign);
+  j.n = nx; j.stride = 1; j.inner = 1; j.outer_stride = nx; j.w = wx;
+  parallel_for((int64_t)ny * nt, axis_range, &j);
+  free(wx);
+  /* y: stride nx, nx pencils per tau plane */
+  cplx* wy = twiddle_table(ny, sign);
+  j.n = ny; j.stride = nx; j.inner = nx; j.outer_stride = (long)nx * ny; j.w = wy;
+  parallel_for((int64_t)nx * nt, axis_range, &j);
+  free(wy);
+  /* tau: stride nx*ny, all nx*ny pencils */
+  cplx* wt = twiddle_table(nt, sign);
+  j.n = nt; j.stride = (long)nx * ny; j.inner = nx * ny; j.outer_stride = 0; j.w = wt;
+  parallel_for((int64_t)nx * ny, axis_range, &j);
+  free(wt);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linear step: A_hat <- exp(dz * Lhat(kx, ky, Omega)) A_hat                   */
+/* ------------------------------------------------------------------------ */
+
+/* 2 pi * numpy.fft.fftfreq(n, d)[m]; bins m >= ceil(n/2) are negative (R7). */
+double orc_angular_freq(int m, int n, double d) {
+  int mm = (m < (n + 1) / 2) ? m : m - n;
+  return ORC_TWO_PI * (double)mm / ((double)n * d);
+}
+
+/* Exponent of the linear operator of field f at (kx, ky, Omega):
+ *  Eq. dispOp with d/dtau -> i Omega and the unitary TOD reading (R2):
+ *     -alpha/2 - i delta Omega + i (k2/2) Omega^2 - i (k3/6) Omega^3
+ *  Eq. diffOp with the sign of R1 and d/dx -> i kx:
+ *     - i (kx^2 + ky^2) / (2 k) - i tan(rho) kx,  k = 2 pi n / lambda.       */
+cplx orc_linear_exponent(const orc_field* fp, double kx, double ky, double om) {
+  double k = ORC_TWO_PI * fp->n / fp->lambda;
+  double re = -0.5 * fp->alpha;
+  double im = -fp->delta * om + 0.5 * fp->k2 * om * om - fp->k3 / 6.0 * om * om * om
+              - (kx * kx + ky * ky) / (2.0 * k) - tan(fp->rho) * kx;
+  return re + I * im;
+}
+
+typedef struct {
+  const orc_problem* pb;
+  cplx* a;  /* one field */
+  const orc_field* fp;
+  double dz;
+} mul_job;
+
+static void mul_range(void* p, int64_t b, int64_t e) {
+  mul_job* j = (mul_job*)p;
+  const orc_problem* pb = j->pb;
+  for (int64_t idx = b; idx < e; ++idx) {
+    int x = (int)(idx % pb->nx);
+    int y = (int)((idx / pb->nx) % pb->ny);
+    int t = (int)(idx / ((int64_t)pb->nx * pb->ny));
+    double kx = orc_angular_freq(x, pb->nx, pb->dx);
+    double ky = orc_angular_freq(y, pb->ny, pb->dy);
+    double om = orc_angular_freq(t, pb->nt, pb->dt);
+    j->a[idx] *= cexp(j->dz * orc_linear_exponent(j->fp, kx, ky, om));
+  }
+}
+
+typedef struct {
+  cplx* a;
+  double s;
+} scale_job;
+static void scale_range(void* p, int64_t b, int64_t e) {
+  scale_job* j = (scale_job*)p;
+  for (int64_t i = b; i < e; ++i) j->a[i] *= j->s;
+}
+
+/* A <- IDFT3( P * DFT3(A) ) for every field (the e^{L dz} factor of Eq. expon). */
+void orc_linear_step(const orc_problem* pb, cplx* fields, double dz) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  for (int f = 0; f < pb->nf; ++f) {
+    cplx* a = fields + f * n;
+    orc_fft3(a, pb->nx, pb->ny, pb->nt, -1);
+    mul_job mj = {pb, a, &pb->f[f], dz};
+    parallel_for(n, mul_range, &mj);
+    orc_fft3(a, pb->nx, pb->ny, pb->nt, +1);
+    scale_job sj = {a, 1.0 / (double)n};
+    parallel_for(n, scale_range, &sj);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonlinear part: right-hand sides of Eqs. CEp/CEs/CEi without L, and RK4.   */
+/* ------------------------------------------------------------------------ */
+
+double orc_kappa(const orc_problem* pb, int f) {
+  return ORC_TWO_PI * pb->d_eff / (pb->f[f].n * pb->f[f].lambda);
+}
+
+/* dA/dz of the coupling terms at one grid point; phi = Phi(z) (R5). */
+static void nl_rhs(int nf, const double* kap, double phi, const cplx* A, cplx* dA) {
+  cplx em = cexp(-I * phi); /* e^{-i Phi} */
+  cplx ep = cexp(I * phi);  /* e^{+i Phi} */
+  if (nf == 3) {
+    dA[0] = I * kap[0] * A[1] * A[2] * em;
+    dA[1] = I * kap[1] * A[0] * conj(A[2]) * ep;
+    dA[2] = I * kap[2] * A[0] * conj(A[1]) * ep;
+  } else { /* (SH, F), R4 */
+    dA[0] = I * (0.5 * kap[0]) * A[1] * A[1] * em;
+    dA[1] = I * kap[1] * A[0] * conj(A[1]) * ep;
+  }
+}
+
+/* Classical RK4 from z_a over h for one point: Phi(z_a + s) = phi_a + dk s. */
+void orc_rk4_point(int nf, const double* kap, double phi_a, double dk, double h, cplx* A) {
+  cplx k1[3], k2[3], k3[3], k4[3], tmp[3];
+  nl_rhs(nf, kap, phi_a, A, k1);
+  for (int f = 0; f < nf; ++f) tmp[f] = A[f] + 0.5 * h * k1[f];
+  nl_rhs(nf, kap, phi_a + dk * 0.5 * h, tmp, k2);
+  for (int f = 0; f < nf; ++f) tmp[f] = A[f] + 0.5 * h * k2[f];
+  nl_rhs(nf, kap, phi_a + dk * 0.5 * h, tmp, k3);
+  for (int f = 0; f < nf; ++f) tmp[f] = A[f] + h * k3[f];
+  nl_rhs(nf, kap, phi_a + dk * h, tmp, k4);
+  for (int f = 0; f < nf; ++f) A[f] += h / 6.0 * (k1[f] + 2.0 * k2[f] + 2.0 * k3[f] + k4[f]);
+}
+
+typedef struct {
+  const orc_problem* pb;
+  cplx* fields;
+  double kap[3];
+  double phi_a, dk, h;
+} nl_job;
+
+static void nl_range(void* p, int64_t b, int64_t e) {
+  nl_job* j = (nl_job*)p;
+  int64_t n = (int64_t)j->pb->nx * j->pb->ny * j->pb->nt;
+  int nf = j->pb->nf;
+  for (int64_t i = b; i < e; ++i) {
+    cplx A[3];
+    for (int f = 0; f < nf; ++f) A[f] = j->fields[f * n + i];
+    orc_rk4_point(nf, j->kap, j->phi_a, j->dk, j->h, A);
+    for (int f = 0; f < nf; ++f) j->fields[f * n + i] = A[f];
+  }
+}
+
+/* N(h): RK4 over [z_a, z_a + h] at every grid point. */
+void orc_nonlinear_step(const orc_problem* pb, cplx* fields, double phi_a, double dk, double h) {
+  nl_job j;
+  j.pb = pb;
+  j.fields = fields;
+  for (int f = 0; f < pb->nf; ++f) j.kap[f] = orc_kappa(pb, f);
+  j.phi_a = phi_a;
+  j.dk = dk;
+  j.h = h;
+  parallel_for((int64_t)pb->nx * pb->ny * pb->nt, nl_range, &j);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Split-step propagation (Eq. expon):  N(dz/2)  L(dz)  N(dz/2)  per step.     */
+/* ------------------------------------------------------------------------ */
+
+/* dk_steps[j] is the mismatch on step j (nz entries).  *phi holds Phi at the
+ * start and is advanced to Phi at the end.  Returns 0, or 5 if the fields
+ * are not finite afterwards (the dz-too-large failure of Sec. 3.2).        */
+int orc_propagate(const orc_problem* pb, cplx* fields, int nz, double dz, const double* dk_steps,
+                  double* phi) {
+  double ph = *phi;
+  for (int j = 0; j < nz; ++j) {
+    double dk = dk_steps[j];
+    orc_nonlinear_step(pb, fields, ph, dk, 0.5 * dz);
+    orc_linear_step(pb, fields, dz);
+    orc_nonlinear_step(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz);
+    ph += dk * dz;
+  }
+  *phi = ph;
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt * pb->nf;
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(creal(fields[i])) || !isfinite(cimag(fields[i]))) return 5;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Energy (Sec. 6):  E = 1/2 c eps0 n sum |A|^2 dx dy dtau, photons = E/(hbar w) */
+/* ------------------------------------------------------------------------ */
+void orc_energy(const orc_problem* pb, const cplx* fields, double* energy, double* photons) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  for (int f = 0; f < pb->nf; ++f) {
+    /* Kahan-compensated sum of |A|^2 */
+    double s = 0.0, c = 0.0;
+    const cplx* a = fields + f * n;
+    for (int64_t i = 0; i < n; ++i) {
+      double v = creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+      double y = v - c;
+      double t = s + y;
+      c = (t - s) - y;
+      s = t;
+    }
+    double e = 0.5 * ORC_C0 * ORC_EPS0 * pb->f[f].n * s * pb->dx * pb->dy * pb->dt;
+    energy[f] = e;
+    if (photons) {
+      double omega = ORC_TWO_PI * ORC_C0 / pb->f[f].lambda;
+      photons[f] = e / (ORC_HBAR * omega);
+    }
+  }
+}
