@@ -1,0 +1,344 @@
+"""Benchmark of the split-step chi(2) solver.
+
+Default workload: OPG, 3 complex64 fields on a 256x256x512 grid (~33.5 M
+points per field), 1000 z-steps of 10 um (walk-off, GVM and GVD on all
+fields, seed-drawn noise on signal and idler).  One bench step = upload of
+the resident input into the solver state, 1000 split steps, energy readout.
+
+Metric: grid-point * field * z-steps per second.  The JSON line also carries
+the roofline of the dominant kernel (CUDA events around every launch, on the
+solver's stream), an end-to-end figure through the C ABI with host buffers,
+SM clocks sampled during the timed region, and the FP64 CPU oracle timed on
+this host's cores on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU (torchrun): every rank runs an independent replica ("replicas
+only": a single split-step instance does not shard on one node here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point·field·z-steps/sec and % of HBM roofline, plain vs batched vs adjoint"
+UNIT = "grid-point·field·z-steps/s"
+KINDS = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2609_08384_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kind):
+    """DRAM bytes per launch of `kind` from the committed ncu summary, or None
+    when the kernels changed since the counters were taken."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    v = d.get("bytes_per_launch", {}).get(kind)
+    return float(v) if v is not None else None
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx = max(mx, float(c[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, c[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(problem, inputs, nz_sample=1):
+    """The FP64 oracle as it stands, on this host's cores, on nz_sample split
+    steps of the same workload."""
+    import oracle
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    prob = oracle.problem_from(problem)
+    t0 = time.perf_counter()
+    oracle.propagate(prob, inputs, nz_sample, problem.dz, problem.dk)
+    dt = time.perf_counter() - t0
+    units = problem.grid.npoints * problem.nfields * nz_sample
+    return {"value": units / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+            "sample": f"{nz_sample} split step(s) of the {problem.name} workload "
+                      f"({problem.nfields} fields, FP64), {dt:.1f} s"}
+
+
+def make_workload(name):
+    from paper_2609_08384_gb300 import workloads as wl
+    if name == "opg":
+        p = wl.problem_opg()
+        return p, wl.inputs_opg(p)
+    if name == "sfg":
+        p = wl.problem_sfg()
+        return p, wl.inputs_sfg(p)
+    if name == "shg":
+        p = wl.problem_shg_small()
+        return p, wl.inputs_shg_small(p)
+    raise ValueError(name)
+
+
+def _dist_init(n_gpus):
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    local = _env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local, dist
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, v, device):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    world, rank, local, dist = _dist_init(args.gpus)
+    if rank != 0:
+        return 0
+    problem, inputs = make_workload(args.config)
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    prob = oracle.problem_from(problem)
+    sample = 1
+    for _ in range(args.warmup):
+        oracle.propagate(prob, inputs, sample, problem.dz, problem.dk)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.propagate(prob, inputs, sample, problem.dz, problem.dk)
+    dt = time.perf_counter() - t0
+    units = problem.grid.npoints * problem.nfields * sample * args.steps
+    v = units / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(problem, args),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+                             "sample": f"{sample} split step of the {problem.name} workload per bench step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(problem, args):
+    g = problem.grid
+    return {"workload": f"{problem.name}_f{problem.nfields}_nz{problem.nz}",
+            "grid_xyt": [g.nx, g.ny, g.nt], "fields": problem.nfields, "nz": problem.nz,
+            "dz_m": problem.dz, "parallelism": f"replicas x{args.gpus}" if args.gpus > 1 else "single instance",
+            "l2": "state (%.0f MB) larger than the 126 MB L2; no flush" % (
+                problem.grid.npoints * problem.nfields * 8 / 1e6)}
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2609_08384_gb300 as br
+
+    world, rank, local, dist = _dist_init(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    problem, inputs = make_workload(args.config)
+    g = problem.grid
+    units_per_step = g.npoints * problem.nfields * problem.nz
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        solver = br.Solver(g, problem.fields, problem.d_eff, problem.dk, stream=stream, device=dev)
+        dev_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).to(dev) for a in inputs]
+    torch.cuda.synchronize(dev)
+
+    def step():
+        solver.set_fields(dev_in)
+        solver.propagate(problem.nz, problem.dz)
+        return solver.energy()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(local)
+    launches0 = solver.launch_count()
+    solver.timing(True)
+    _barrier(dist)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    _barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    kind_ms, kind_n = solver.timing(False)
+    launches = solver.launch_count() - launches0
+    ms_max = _max_over_ranks(dist, ms, dev)
+    value = world * units_per_step * args.steps / (ms_max / 1e3)
+
+    # roofline of the dominant kernel: algorithmic bytes = one read and one
+    # write of every field's state per launch (16 B per grid point per field)
+    main = int(np.argmax(kind_ms[:4]))
+    alg_bytes = 16.0 * g.npoints * problem.nfields
+    avg_s = kind_ms[main] / max(1, kind_n[main]) / 1e3
+    peak, peak_kind = _peaks()
+    achieved = alg_bytes / avg_s / 1e9
+    traffic = _traffic(KINDS[main])
+    roofline = {"bound": "hbm", "kernel": KINDS[main], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy)",
+                "alg_bytes_per_launch": alg_bytes}
+    total_k = float(np.sum(kind_ms))
+    kernels = {KINDS[k]: {"ms_total": float(kind_ms[k]), "launches": int(kind_n[k]),
+                          "us_per_launch": float(1e3 * kind_ms[k] / max(1, kind_n[k])),
+                          "share": float(kind_ms[k] / total_k) if total_k else 0.0,
+                          "GB_per_s_alg": float(alg_bytes / (kind_ms[k] / max(1, kind_n[k]) / 1e3) / 1e9)
+                          if k < 4 and kind_n[k] else None}
+               for k in range(5)}
+    step_alg_gbs = 16.0 * units_per_step * args.steps / (ms / 1e3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).pin_memory() for a in inputs]
+    host_out = [torch.empty_like(h).pin_memory() for h in host_in]
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        solver.set_fields(host_in)
+        solver.propagate(problem.nz, problem.dz)
+        solver.get_fields(out=host_out)
+    t_e2e = time.perf_counter() - t0
+    t_e2e = _max_over_ranks(dist, t_e2e, dev)
+    nbytes = g.npoints * problem.nfields * 8
+    e2e = {"value": world * units_per_step * e2e_steps / t_e2e, "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    solver.close()
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(problem, inputs, 1)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(problem, args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
+            "step_hbm": {"alg_GB_per_s": step_alg_gbs, "alg_bytes_per_point_field_step": 16,
+                         "moved_bytes_per_point_field_step_design": 64},
+            "forms": {"plain": value}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="opg", choices=["opg", "sfg", "shg"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,142 @@
+/*
+ * brahms.h -- C ABI of the GB300 split-step solver for the coupled chi(2)
+ * three-wave-mixing equations in (3+1)D.
+ *
+ * The solver advances the slowly varying envelopes A_f(x, y, tau) of two
+ * (degenerate SHG: SH, F) or three (p, s, i) fields along z with the
+ * symmetric split step of Sec. 3.1 (Eq. expon):
+ *     A(z+dz) = N(dz/2) IDFT3{ P(dz) DFT3{ N(dz/2) A(z) } },
+ * where N is one classical RK4 step over dz/2 of the coupling terms of
+ * Eqs. CEp/CEs/CEi (Sec. 2) and P is the linear propagator of Eqs. dispOp and
+ * diffOp.  Conventions fixed by this library where the paper is silent:
+ *   - diffraction enters as +(i/2k) transverse Laplacian (the sign that the
+ *     paper's focused Gaussian beam, Eq. gaussianbeam, solves);
+ *   - third-order dispersion is the unitary -[... - (k3/6) d^3/dtau^3];
+ *   - two-field SHG: dA_SH/dz = i (kappa_SH/2) A_F^2 e^{-i Phi},
+ *                    dA_F/dz  = i kappa_F A_SH A_F^* e^{+i Phi};
+ *   - Phi(z) is the integral of Delta k; the first RK4 half step spans
+ *     [z_j, z_j+dz/2], the second [z_j+dz/2, z_j+dz];
+ *   - grid x_j = (j - N/2) dx, angular frequencies 2 pi fftfreq(N, d) with
+ *     the Nyquist bin negative, forward DFT e^{-2 pi i m n/N}.
+ *
+ * Layout of every field buffer: complex [nt][ny][nx], x fastest (Sec. 4.1,
+ * the IDX(x, y, tau) ordering), interleaved (re, im).  Units are SI.
+ *
+ * Errors: no call aborts; each returns a brahms_status and stores a message
+ * retrievable with brahms_last_error(ctx).  Calls on one context are not
+ * thread-safe.  Device work is enqueued on the context's CUDA stream.
+ */
+#ifndef BRAHMS_H
+#define BRAHMS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BRAHMS_OK = 0,
+  BRAHMS_E_ARG = 1,       /* invalid argument (null pointer, bad count, non-finite value) */
+  BRAHMS_E_SIZE = 2,      /* grid length not supported (must be one of the FFT lengths) */
+  BRAHMS_E_CUDA = 3,      /* a CUDA runtime call failed */
+  BRAHMS_E_OOM = 4,       /* device allocation failed or workspace too small */
+  BRAHMS_E_NONFINITE = 5, /* fields became non-finite: dz too large (Sec. 3.2) */
+  BRAHMS_E_TIMEOUT = 6,   /* a bounded device-side wait expired */
+  BRAHMS_E_STATE = 7      /* call out of order (e.g. propagate before set_fields) */
+} brahms_status;
+
+enum { BRAHMS_C64 = 0, BRAHMS_C128 = 1 };
+
+/* Per-field linear coefficients, SI (Eqs. dispOp, diffOp; kappa = 2 pi d_eff/(n lambda)). */
+typedef struct {
+  double lambda; /* vacuum wavelength [m] */
+  double n;      /* refractive index */
+  double delta;  /* group-velocity mismatch 1/v_s - 1/v_f [s/m] */
+  double k2;     /* group-velocity dispersion [s^2/m] */
+  double k3;     /* third-order dispersion [s^3/m] */
+  double rho;    /* walk-off angle [rad] */
+  double alpha;  /* linear loss [1/m] */
+} brahms_field_params;
+
+typedef struct brahms_ctx brahms_ctx;
+
+/* Bytes of device workspace a context of this shape needs (fields, tables,
+ * reduction partials).  Pass this much to brahms_init_grid, or NULL there to
+ * let the library allocate it.  Returns E_SIZE / E_ARG for bad shapes. */
+brahms_status brahms_workspace_size(int nx, int ny, int nt, int nfields, size_t* bytes);
+
+/* Create a context.  nx, ny, nt: grid lengths, each one of 2,4,...,4096 or
+ * 3*2^k for 6 <= 3*2^k <= 768 (else E_SIZE).  dx, dy [m], dt [s]: spacings > 0.
+ * nfields: 2 (SH, F) or 3 (p, s, i); fp: nfields coefficient records.
+ * d_eff [m/V]; dk [1/m]: constant mismatch Delta k = k_p - k_s - k_i (Eq. mismatch).
+ * workspace: device memory of at least brahms_workspace_size() bytes, 256-byte
+ * aligned, owned by the caller and kept alive until brahms_free; or NULL.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out owns the context; free it with brahms_free. */
+brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double dx, double dy, double dt,
+                               int nfields, const brahms_field_params* fp, double d_eff, double dk,
+                               void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* Copy the initial envelopes in.  fields: nfields pointers, each to nt*ny*nx
+ * complex values of dtype BRAHMS_C64 (float pairs) or BRAHMS_C128 (double
+ * pairs), on the device if on_device != 0 else in host memory.  Resets z and
+ * Phi to zero.  Host copies are complete when the call returns; device copies
+ * are ordered on the context stream.  Non-finite host input gives E_ARG. */
+brahms_status brahms_set_fields(brahms_ctx* ctx, const void* const* fields, int dtype, int on_device);
+
+/* Piecewise mismatch profile: step j (counted from the last set_fields) uses
+ * dk[j] for j < n and the constant dk afterwards; n = 0 clears it.  The
+ * library copies the array. */
+brahms_status brahms_set_dk_profile(brahms_ctx* ctx, const double* dk, int n);
+
+/* Advance nz >= 0 split steps of length dz > 0 [m] (Sec. 3.1).  Asynchronous:
+ * work is enqueued on the context stream; z and Phi accumulate in the
+ * context.  A non-finite result is reported by the next synchronising call
+ * (brahms_sync, brahms_get_fields, brahms_energy) as E_NONFINITE. */
+brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz);
+
+/* Copy the current envelopes out (same conventions as set_fields); waits
+ * for the stream. */
+brahms_status brahms_get_fields(brahms_ctx* ctx, void* const* out, int dtype, int on_device);
+
+/* Per-field pulse energy E_f = 1/2 c eps0 n_f sum |A_f|^2 dx dy dtau [J]
+ * (Sec. 6, the power integral over tau) and photon number E_f/(hbar w_f)
+ * (photons may be NULL).  FP64 accumulation; waits for the stream; returns
+ * E_NONFINITE if any field is not finite. */
+brahms_status brahms_energy(brahms_ctx* ctx, double* energy_j, double* photons);
+
+/* Wait for the context stream; reports CUDA errors and E_NONFINITE. */
+brahms_status brahms_sync(brahms_ctx* ctx);
+
+/* Diagnostic: apply the unnormalised forward 3D DFT (direction -1) or the
+ * normalised inverse (direction +1) to the state in place. */
+brahms_status brahms_transform(brahms_ctx* ctx, int direction);
+
+/* Current propagation distance [m] and accumulated mismatch phase [rad]. */
+brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
+
+/* Per-kernel timing with CUDA events on the context stream.  enable != 0
+ * starts recording (and clears previous records); enable == 0 stops.  With
+ * ms/launches non-NULL the accumulated device time [ms] and launch count of
+ * each kernel kind (0 x-pass, 1 y-pass forward, 2 tau-pass, 3 y-pass inverse,
+ * 4 other) are written to the first nkinds entries; this waits for the stream. */
+brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* launches, int nkinds);
+
+/* Number of kernel launches this context has enqueued since creation. */
+long long brahms_launch_count(const brahms_ctx* ctx);
+
+/* Release the context and any memory the library allocated for it. */
+void brahms_free(brahms_ctx* ctx);
+
+/* Last error message of ctx ("" if none); a static string if ctx is NULL. */
+const char* brahms_last_error(const brahms_ctx* ctx);
+
+/* Name of a status code. */
+const char* brahms_status_string(brahms_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BRAHMS_H */

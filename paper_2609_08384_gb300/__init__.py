@@ -1,0 +1,256 @@
+"""Python binding of the GB300 split-step chi(2) solver (C ABI in include/brahms.h).
+
+Argument marshalling only: every step of the split-step path runs in the CUDA
+library ``_build/libbrahms.so``.  PyTorch provides device memory (the
+workspace), CUDA streams and pinned host buffers.  If the library has not
+been built, importing the binding works but every call raises -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbrahms.so")
+
+BRAHMS_OK = 0
+BRAHMS_E_ARG = 1
+BRAHMS_E_SIZE = 2
+BRAHMS_E_CUDA = 3
+BRAHMS_E_OOM = 4
+BRAHMS_E_NONFINITE = 5
+BRAHMS_E_TIMEOUT = 6
+BRAHMS_E_STATE = 7
+BRAHMS_C64 = 0
+BRAHMS_C128 = 1
+
+KIND_NAMES = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
+
+# Every entry point declared in include/brahms.h, with its ctypes signature.
+_c = ctypes
+_vp = _c.c_void_p
+_dp = _c.POINTER(_c.c_double)
+_llp = _c.POINTER(_c.c_longlong)
+
+
+class FieldParams(ctypes.Structure):
+    _fields_ = [("lambda_", _c.c_double), ("n", _c.c_double), ("delta", _c.c_double), ("k2", _c.c_double),
+                ("k3", _c.c_double), ("rho", _c.c_double), ("alpha", _c.c_double)]
+
+
+SIGNATURES = {
+    "brahms_workspace_size": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "brahms_init_grid": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double,
+                                    _c.c_double, _c.c_int, _c.POINTER(FieldParams), _c.c_double, _c.c_double,
+                                    _vp, _c.c_size_t, _vp]),
+    "brahms_set_fields": (_c.c_int, [_vp, _c.POINTER(_vp), _c.c_int, _c.c_int]),
+    "brahms_set_dk_profile": (_c.c_int, [_vp, _dp, _c.c_int]),
+    "brahms_propagate": (_c.c_int, [_vp, _c.c_int, _c.c_double]),
+    "brahms_get_fields": (_c.c_int, [_vp, _c.POINTER(_vp), _c.c_int, _c.c_int]),
+    "brahms_energy": (_c.c_int, [_vp, _dp, _dp]),
+    "brahms_sync": (_c.c_int, [_vp]),
+    "brahms_transform": (_c.c_int, [_vp, _c.c_int]),
+    "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
+    "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
+    "brahms_launch_count": (_c.c_longlong, [_vp]),
+    "brahms_free": (None, [_vp]),
+    "brahms_last_error": (_c.c_char_p, [_vp]),
+    "brahms_status_string": (_c.c_char_p, [_c.c_int]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+class BrahmsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{status_string(status) if _lib else status}: {msg}")
+        self.status = status
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def load(path: Optional[str] = None):
+    """Load the CUDA library (raises if it is missing: no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} (run __graft_entry__.build())")
+            lib = ctypes.CDLL(p)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def status_string(s: int) -> str:
+    return load().brahms_status_string(int(s)).decode()
+
+
+def _check(ctx, s: int):
+    if s != BRAHMS_OK:
+        msg = load().brahms_last_error(ctx).decode() if ctx else ""
+        raise BrahmsError(s, msg)
+
+
+def _ptr_array(ptrs: Sequence[int]):
+    arr = (_vp * len(ptrs))(*[_vp(int(p)) for p in ptrs])
+    return arr
+
+
+def field_params(fp) -> FieldParams:
+    """FieldParams from a workloads.FieldParams (or any object with as_tuple())."""
+    return FieldParams(*fp.as_tuple())
+
+
+def workspace_size(nx: int, ny: int, nt: int, nfields: int) -> int:
+    b = ctypes.c_size_t()
+    _check(None, load().brahms_workspace_size(nx, ny, nt, nfields, ctypes.byref(b)))
+    return int(b.value)
+
+
+class Solver:
+    """One simulation context: a torch-owned device workspace plus the C
+    context.  Methods map one-to-one onto the C entry points."""
+
+    def __init__(self, grid, fields, d_eff: float, dk: float, stream=None, device=None):
+        import torch
+
+        lib = load()
+        self.nf = len(fields)
+        self.grid = grid
+        self.shape = (grid.nt, grid.ny, grid.nx)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        nbytes = workspace_size(grid.nx, grid.ny, grid.nt, self.nf)
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        fp = (FieldParams * 3)(*[field_params(f) for f in fields])
+        ctx = _vp()
+        s = lib.brahms_init_grid(ctypes.byref(ctx), grid.nx, grid.ny, grid.nt, grid.dx, grid.dy, grid.dt,
+                                 self.nf, fp, float(d_eff), float(dk), _vp(aligned), nbytes,
+                                 _vp(self.stream.cuda_stream))
+        _check(None, s)
+        self.ctx = ctx
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().brahms_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points
+    def set_fields(self, fields, on_device: Optional[bool] = None):
+        """fields: sequence of torch tensors (cuda or cpu) or numpy arrays,
+        complex64 or complex128, shape (nt, ny, nx), C-contiguous."""
+        ptrs, dtype, dev = self._marshal(fields, on_device)
+        _check(self.ctx, load().brahms_set_fields(self.ctx, _ptr_array(ptrs), dtype, int(dev)))
+
+    def get_fields(self, out=None, dtype=np.complex64, on_device: bool = False):
+        """Returns a list of arrays (numpy on host, torch on device) unless out is given."""
+        import torch
+
+        if out is None:
+            if on_device:
+                tdt = torch.complex64 if np.dtype(dtype) == np.complex64 else torch.complex128
+                out = [torch.empty(self.shape, dtype=tdt, device=self.device) for _ in range(self.nf)]
+            else:
+                out = [np.empty(self.shape, dtype=dtype) for _ in range(self.nf)]
+        ptrs, dt, dev = self._marshal(out, on_device, writable=True)
+        _check(self.ctx, load().brahms_get_fields(self.ctx, _ptr_array(ptrs), dt, int(dev)))
+        return out
+
+    def set_dk_profile(self, dk):
+        arr = np.ascontiguousarray(dk, dtype=np.float64)
+        _check(self.ctx, load().brahms_set_dk_profile(self.ctx, arr.ctypes.data_as(_dp), int(arr.size)))
+
+    def propagate(self, nz: int, dz: float):
+        _check(self.ctx, load().brahms_propagate(self.ctx, int(nz), float(dz)))
+
+    def energy(self):
+        e = np.zeros(self.nf)
+        ph = np.zeros(self.nf)
+        _check(self.ctx, load().brahms_energy(self.ctx, e.ctypes.data_as(_dp), ph.ctypes.data_as(_dp)))
+        return e, ph
+
+    def sync(self):
+        _check(self.ctx, load().brahms_sync(self.ctx))
+
+    def transform(self, direction: int):
+        _check(self.ctx, load().brahms_transform(self.ctx, int(direction)))
+
+    def get_z(self):
+        z = ctypes.c_double()
+        phi = ctypes.c_double()
+        _check(self.ctx, load().brahms_get_z(self.ctx, ctypes.byref(z), ctypes.byref(phi)))
+        return z.value, phi.value
+
+    def timing(self, enable: bool):
+        ms = np.zeros(5)
+        n = np.zeros(5, dtype=np.int64)
+        _check(self.ctx, load().brahms_timing(self.ctx, int(enable), ms.ctypes.data_as(_dp),
+                                              n.ctypes.data_as(_llp), 5))
+        return ms, n
+
+    def launch_count(self) -> int:
+        return int(load().brahms_launch_count(self.ctx))
+
+    # -- helpers
+    def _marshal(self, arrs, on_device, writable=False):
+        import torch
+
+        if len(arrs) != self.nf:
+            raise ValueError(f"expected {self.nf} fields")
+        ptrs = []
+        kinds = set()
+        dev = None
+        for a in arrs:
+            if isinstance(a, torch.Tensor):
+                if tuple(a.shape) != self.shape or not a.is_contiguous():
+                    raise ValueError("field tensors must be contiguous with shape (nt, ny, nx)")
+                kinds.add(a.dtype)
+                d = a.is_cuda
+                ptrs.append(a.data_ptr())
+            else:
+                if not isinstance(a, np.ndarray) or a.shape != self.shape or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("field arrays must be C-contiguous numpy arrays of shape (nt, ny, nx)")
+                if writable and not a.flags["WRITEABLE"]:
+                    raise ValueError("output array is read-only")
+                kinds.add(torch.complex64 if a.dtype == np.complex64 else
+                          torch.complex128 if a.dtype == np.complex128 else a.dtype)
+                d = False
+                ptrs.append(a.ctypes.data)
+            if dev is None:
+                dev = d
+            elif dev != d:
+                raise ValueError("all fields must be on the same side (host or device)")
+        if on_device is not None and bool(on_device) != bool(dev):
+            raise ValueError("on_device does not match the buffers")
+        if len(kinds) != 1:
+            raise ValueError("all fields must share one dtype")
+        k = kinds.pop()
+        if k == torch.complex64:
+            dt = BRAHMS_C64
+        elif k == torch.complex128:
+            dt = BRAHMS_C128
+        else:
+            raise ValueError("fields must be complex64 or complex128")
+        return ptrs, dt, dev

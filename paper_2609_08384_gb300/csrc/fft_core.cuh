@@ -1,0 +1,274 @@
+// Register-resident mixed-radix Stockham FFT building blocks for sm_103a.
+//
+// A pencil of length N is owned by T = N/E threads; each thread keeps E
+// complex values in registers.  One Stockham pass of radix R (Govindaraju et
+// al., "High performance discrete Fourier transforms on graphics processors",
+// SC'08, autosort formulation) reads the R inputs j + r N/R of butterfly j,
+// multiplies by W_N^{r (j mod Ns) N/(Ns R)}, applies a radix-R DFT and writes
+// the results to (j/Ns) Ns R + (j mod Ns) + r Ns.  Between passes the values
+// are exchanged through shared memory; the first pass reads its inputs
+// straight from global memory and the last pass leaves the outputs in
+// registers at positions j + r N/R_last, so a kernel stores them with
+// coalesced writes and never stages the whole pencil twice.
+//
+// The forward transform is unnormalised with e^{-2 pi i m n / N}; the inverse
+// uses e^{+...} and the radix order reversed, so that the inverse's first
+// pass reads exactly the positions the forward's last pass produced.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace brahms {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward sign) or +i (inverse sign)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// multiply by the constant W = cos(theta) -/+ i sin(theta) (forward uses minus)
+template <bool INV>
+__device__ __forceinline__ float2 twc(float2 a, float c, float s) {
+  return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
+             : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
+}
+
+constexpr float kS2 = 0.70710678118654752440f;   // cos(pi/4)
+constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
+constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
+constexpr float kS3 = 0.86602540378443864676f;   // sin(pi/3)
+
+// ---------------------------------------------------------------- codelets
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& v0, float2& v1, float2& v2, float2& v3) {
+  float2 a = cadd(v0, v2), b = csub(v0, v2), c = cadd(v1, v3), d = rot90<INV>(csub(v1, v3));
+  v0 = cadd(a, c);
+  v2 = csub(a, c);
+  v1 = cadd(b, d);
+  v3 = csub(b, d);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& v0, float2& v1, float2& v2) {
+  float2 s = cadd(v1, v2);
+  float2 t = make_float2(fmaf(-0.5f, s.x, v0.x), fmaf(-0.5f, s.y, v0.y));
+  float2 u = rot90<INV>(cscale(csub(v1, v2), kS3));
+  v0 = cadd(v0, s);
+  v1 = cadd(t, u);
+  v2 = csub(t, u);
+}
+
+// radix 8 = 2 x 4: n = 4 n1 + n2, k = k1 + 2 k2
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  float2 y0[4], y1[4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    y0[n2] = cadd(v[n2], v[n2 + 4]);
+    y1[n2] = csub(v[n2], v[n2 + 4]);
+  }
+  y1[1] = twc<INV>(y1[1], kS2, kS2);
+  y1[2] = rot90<INV>(y1[2]);
+  y1[3] = twc<INV>(y1[3], -kS2, kS2);
+  dft4<INV>(y0[0], y0[1], y0[2], y0[3]);
+  dft4<INV>(y1[0], y1[1], y1[2], y1[3]);
+#pragma unroll
+  for (int k2 = 0; k2 < 4; ++k2) {
+    v[2 * k2] = y0[k2];
+    v[2 * k2 + 1] = y1[k2];
+  }
+}
+
+// multiply by W16^e, e in [0, 9]
+template <bool INV, int E>
+__device__ __forceinline__ float2 w16(float2 a) {
+  if constexpr (E == 0) return a;
+  else if constexpr (E == 1) return twc<INV>(a, kC16, kS16);
+  else if constexpr (E == 2) return twc<INV>(a, kS2, kS2);
+  else if constexpr (E == 3) return twc<INV>(a, kS16, kC16);
+  else if constexpr (E == 4) return rot90<INV>(a);
+  else if constexpr (E == 6) return twc<INV>(a, -kS2, kS2);
+  else if constexpr (E == 9) return twc<INV>(a, -kC16, -kS16);
+  else return a;
+}
+
+// radix 16 = 4 x 4: n = 4 n1 + n2, k = k1 + 4 k2
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* v) {
+  float2 y[4][4];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 a0 = v[n2], a1 = v[4 + n2], a2 = v[8 + n2], a3 = v[12 + n2];
+    dft4<INV>(a0, a1, a2, a3);
+    y[n2][0] = a0;
+    y[n2][1] = a1;
+    y[n2][2] = a2;
+    y[n2][3] = a3;
+  }
+  y[1][1] = w16<INV, 1>(y[1][1]);
+  y[1][2] = w16<INV, 2>(y[1][2]);
+  y[1][3] = w16<INV, 3>(y[1][3]);
+  y[2][1] = w16<INV, 2>(y[2][1]);
+  y[2][2] = w16<INV, 4>(y[2][2]);
+  y[2][3] = w16<INV, 6>(y[2][3]);
+  y[3][1] = w16<INV, 3>(y[3][1]);
+  y[3][2] = w16<INV, 6>(y[3][2]);
+  y[3][3] = w16<INV, 9>(y[3][3]);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
+    dft4<INV>(b0, b1, b2, b3);
+    v[k1] = b0;
+    v[k1 + 4] = b1;
+    v[k1 + 8] = b2;
+    v[k1 + 12] = b3;
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft(float2* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+  else static_assert(R == 2, "unsupported radix");
+}
+
+// ------------------------------------------------------------------- plans
+// Forward radix sequence and registers per thread (E, a multiple of every
+// radix) for each supported length.
+template <int N>
+struct FftPlan;
+#define BRAHMS_PLAN(N_, E_, NP_, R0_, R1_, R2_, R3_)                          \
+  template <>                                                                \
+  struct FftPlan<N_> {                                                       \
+    static constexpr int NP = NP_;                                           \
+    static constexpr int E = E_;                                             \
+    static constexpr int r(int p) {                                          \
+      return p == 0 ? R0_ : p == 1 ? R1_ : p == 2 ? R2_ : R3_;               \
+    }                                                                        \
+  };
+BRAHMS_PLAN(2, 2, 1, 2, 0, 0, 0)
+BRAHMS_PLAN(4, 4, 1, 4, 0, 0, 0)
+BRAHMS_PLAN(8, 8, 1, 8, 0, 0, 0)
+BRAHMS_PLAN(16, 16, 1, 16, 0, 0, 0)
+BRAHMS_PLAN(32, 8, 2, 4, 8, 0, 0)
+BRAHMS_PLAN(64, 8, 2, 8, 8, 0, 0)
+BRAHMS_PLAN(128, 16, 2, 16, 8, 0, 0)
+BRAHMS_PLAN(256, 16, 2, 16, 16, 0, 0)
+BRAHMS_PLAN(512, 16, 3, 8, 8, 8, 0)
+BRAHMS_PLAN(1024, 16, 3, 16, 8, 8, 0)
+BRAHMS_PLAN(2048, 16, 3, 16, 16, 8, 0)
+BRAHMS_PLAN(4096, 16, 3, 16, 16, 16, 0)
+BRAHMS_PLAN(6, 6, 2, 3, 2, 0, 0)
+BRAHMS_PLAN(12, 12, 2, 3, 4, 0, 0)
+BRAHMS_PLAN(24, 24, 2, 3, 8, 0, 0)
+BRAHMS_PLAN(48, 12, 3, 3, 4, 4, 0)
+BRAHMS_PLAN(96, 24, 3, 3, 4, 8, 0)
+BRAHMS_PLAN(192, 24, 3, 3, 8, 8, 0)
+BRAHMS_PLAN(384, 24, 4, 3, 8, 4, 4)
+BRAHMS_PLAN(768, 48, 3, 3, 16, 16, 0)
+#undef BRAHMS_PLAN
+
+template <int N, bool INV>
+__host__ __device__ constexpr int fft_radix(int p) {
+  return INV ? FftPlan<N>::r(FftPlan<N>::NP - 1 - p) : FftPlan<N>::r(p);
+}
+template <int N, bool INV>
+__host__ __device__ constexpr int fft_ns(int p) {
+  int s = 1;
+  for (int q = 0; q < p; ++q) s *= fft_radix<N, INV>(q);
+  return s;
+}
+// position of input r of butterfly j in the first pass
+template <int N, bool INV>
+__host__ __device__ constexpr int fft_in_stride() { return N / fft_radix<N, INV>(0); }
+// position of output r of butterfly j after the last pass
+template <int N, bool INV>
+__host__ __device__ constexpr int fft_out_stride() { return N / fft_radix<N, INV>(FftPlan<N>::NP - 1); }
+
+// ---------------------------------------------------------------- exchange
+// Contiguous pencil (one row of x): one padding slot per 16 entries.
+struct XchRow {
+  float2* base;
+  __device__ __forceinline__ void st(int pos, float2 v) const { base[pos + (pos >> 4)] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return base[pos + (pos >> 4)]; }
+  __host__ __device__ static constexpr int pitch(int n) { return n + n / 16 + 1; }
+};
+// Strided pencils: TX neighbouring columns, column index fastest.
+template <int TX>
+struct XchCol {
+  float2* base;
+  int tx;
+  __device__ __forceinline__ void st(int pos, float2 v) const { base[pos * TX + tx] = v; }
+  __device__ __forceinline__ float2 ld(int pos) const { return base[pos * TX + tx]; }
+};
+
+// Passes P..NP-1 of a length-N transform on the registers v (see header).
+// Every thread of the CTA must call this (it contains __syncthreads()).
+template <int N, bool INV, int P, class X>
+__device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const X& x,
+                                        const float2* __restrict__ tw) {
+  constexpr int NP = FftPlan<N>::NP;
+  constexpr int E = FftPlan<N>::E;
+  constexpr int T = N / E;
+  constexpr int R = fft_radix<N, INV>(P);
+  constexpr int NS = fft_ns<N, INV>(P);
+  constexpr int B = E / R;
+  static_assert(E % R == 0, "E must be a multiple of every radix");
+  if constexpr (NS > 1) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * T;
+      const int m = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const float2 w = tw[r * m * (N / (NS * R))];
+        v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < B; ++b) dft<R, INV>(&v[b * R]);
+  if constexpr (P + 1 < NP) {
+    constexpr int R2 = fft_radix<N, INV>(P + 1);
+    constexpr int B2 = E / R2;
+    __syncthreads();  // earlier readers of the exchange buffer are done
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * T;
+      const int m = j % NS;
+      const int d = (j / NS) * NS * R + m;
+#pragma unroll
+      for (int r = 0; r < R; ++r) x.st(d + r * NS, v[b * R + r]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < B2; ++b) {
+      const int j = t + b * T;
+#pragma unroll
+      for (int r = 0; r < R2; ++r) v[b * R2 + r] = x.ld(j + r * (N / R2));
+    }
+    fft_run<N, INV, P + 1>(v, t, x, tw);
+  }
+}
+
+}  // namespace brahms

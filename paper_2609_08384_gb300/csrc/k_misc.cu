@@ -1,0 +1,149 @@
+// Set-up tables, the energy reduction and dtype conversions.
+#include "kernels.cuh"
+
+namespace brahms {
+
+// tw[k] = exp(-2 pi i k / n), evaluated in FP64 and rounded once to FP32.
+__global__ void twiddle_kernel(float2* tw, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) {
+    double s, c;
+    sincospi(-2.0 * (double)k / (double)n, &s, &c);
+    tw[k] = make_float2((float)c, (float)s);
+  }
+}
+
+cudaError_t run_twiddles(float2* tw, int n, cudaStream_t s) {
+  twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  return cudaPeekAtLastError();
+}
+
+// 2 pi * numpy.fft.fftfreq(n, d)[m]; the Nyquist bin is negative.
+__device__ __forceinline__ double ang_freq(int m, int n, double d) {
+  const int mm = (m < (n + 1) / 2) ? m : m - n;
+  return 6.283185307179586476925286766559 * (double)mm / ((double)n * d);
+}
+
+// exp(i phi) with the FP64 phase reduced to [-pi, pi] before the FP32 sincos.
+__device__ __forceinline__ float2 unit_phase(double phi, double amp) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const double r = phi - two_pi * rint(phi / two_pi);
+  float s, c;
+  sincosf((float)r, &s, &c);
+  return make_float2((float)amp * c, (float)amp * s);
+}
+
+// Separable factors of the linear propagator over dz (Eqs. dispOp, diffOp,
+// with d/dx -> i kx, d/dtau -> i Omega, diffraction +(i/2k) Laplacian and the
+// unitary third-order term):
+//   Px = exp(-i dz [kx^2/(2k) + tan(rho) kx])
+//   Py = exp(-i dz ky^2/(2k))
+//   Pt = exp(dz [-alpha/2 - i delta Omega + i k2/2 Omega^2 - i k3/6 Omega^3])
+__global__ void prop_tables_kernel(const TableArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int per = a.nx + a.ny + a.nt;
+  if (i >= per * a.nf) return;
+  const int f = i / per;
+  int m = i % per;
+  if (m < a.nx) {
+    const double kx = ang_freq(m, a.nx, a.dx);
+    const double ph = -a.dz * (kx * kx / (2.0 * a.k[f]) + tan(a.rho[f]) * kx);
+    a.px[f * a.nx + m] = unit_phase(ph, 1.0);
+    return;
+  }
+  m -= a.nx;
+  if (m < a.ny) {
+    const double ky = ang_freq(m, a.ny, a.dy);
+    a.py[f * a.ny + m] = unit_phase(-a.dz * ky * ky / (2.0 * a.k[f]), 1.0);
+    return;
+  }
+  m -= a.ny;
+  const double om = ang_freq(m, a.nt, a.dt);
+  const double ph = a.dz * (-a.delta[f] * om + 0.5 * a.k2[f] * om * om - a.k3[f] / 6.0 * om * om * om);
+  a.pt[f * a.nt + m] = unit_phase(ph, exp(-0.5 * a.alpha[f] * a.dz));
+}
+
+cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s) {
+  const int n = (a.nx + a.ny + a.nt) * a.nf;
+  prop_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+// ------------------------------------------------------------- energy
+// Per-field sum of |A|^2 in FP64 (each square taken in FP64 too).
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) energy_partial_kernel(const float2* __restrict__ data, long long n,
+                                                             long long fstride, double* partial) {
+  const float2* a = data + blockIdx.y * fstride;
+  double s = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = a[i];
+    s = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, s));
+  }
+  __shared__ double red[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) energy_final_kernel(const double* partial, int nblocks, double* out) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partial[blockIdx.x * nblocks + i];
+  __shared__ double red[8];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) out[blockIdx.x] = v;
+  }
+}
+
+cudaError_t run_energy(const float2* data, long long n, int nf, long long fstride, double* partial,
+                       int nblocks, double* out, cudaStream_t s) {
+  energy_partial_kernel<<<dim3(nblocks, nf), 256, 0, s>>>(data, n, fstride, partial);
+  energy_final_kernel<<<nf, 256, 0, s>>>(partial, nblocks, out);
+  return cudaPeekAtLastError();
+}
+
+// ---------------------------------------------------------- conversions
+__global__ void c128_to_c64_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = in[i];
+    out[i] = make_float2((float)v.x, (float)v.y);
+  }
+}
+__global__ void c64_to_c128_kernel(const float2* __restrict__ in, double2* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 v = in[i];
+    out[i] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+static int grid_for(long long n) {
+  long long g = (n + 255) / 256;
+  return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
+}
+
+cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s) {
+  c128_to_c64_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  return cudaPeekAtLastError();
+}
+cudaError_t run_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t s) {
+  c64_to_c128_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace brahms

@@ -1,0 +1,46 @@
+// x-pass instantiations and dispatch.
+#include "kernels.cuh"
+
+namespace brahms {
+
+template <int NX, int F>
+static cudaError_t launch_x(const XPassArgs& a, cudaStream_t s) {
+  constexpr int ROWS = xpass_rows<NX>();
+  constexpr int THREADS = ROWS * fft_threads<NX>();
+  const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(xpass_kernel<NX, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const long long grid = (a.rows + ROWS - 1) / ROWS;
+  if (grid <= 0) return cudaSuccess;
+  xpass_kernel<NX, F><<<(unsigned)grid, THREADS, smem, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_xpass(int nx, int nf, const XPassArgs& a, cudaStream_t s) {
+  switch (nx) {
+#define BRAHMS_X_CASE(N) \
+  case N:                \
+    return nf == 3 ? launch_x<N, 3>(a, s) : launch_x<N, 2>(a, s);
+    BRAHMS_FOR_EACH_SIZE(BRAHMS_X_CASE)
+#undef BRAHMS_X_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+bool size_supported(int n) {
+  switch (n) {
+#define BRAHMS_S_CASE(N) case N:
+    BRAHMS_FOR_EACH_SIZE(BRAHMS_S_CASE)
+#undef BRAHMS_S_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+}  // namespace brahms

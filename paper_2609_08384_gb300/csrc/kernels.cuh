@@ -1,0 +1,378 @@
+// Kernels of one split-step z-step (Sec. 3.1, Eq. expon) on the layout
+// fields[f][tau][y][x] (x fastest), complex64.
+//
+// A z-step is four HBM passes per field:
+//   x-pass  inverse x-FFT, the second RK4 half step of step j, the first RK4
+//           half step of step j+1, forward x-FFT (all fields of a row at once,
+//           the nonlinear coupling is pointwise across fields)
+//   y-pass  forward y-FFT
+//   t-pass  forward tau-FFT, multiply by the linear propagator
+//           P = Px(kx) Py(ky) Pt(Omega) / (NX NY NT), inverse tau-FFT
+//   y-pass  inverse y-FFT
+// Between calls the state is in real space; the first and the last step of
+// a call peel the x-pass (NL_FIRST / NL_LAST).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace brahms {
+
+enum XMode : int { XM_FWD = 0, XM_INV = 1, XM_NL_FIRST = 2, XM_NL_MID = 3, XM_NL_LAST = 4 };
+
+struct XPassArgs {
+  float2* data;        // [nf][rows][nx]
+  long long fstride;   // elements between fields
+  long long rows;      // ny * nt
+  const float2* tw;    // e^{-2 pi i k / nx}, k < nx
+  int mode;            // XMode
+  double phiA, dkA;    // step whose first half is applied: Phi(z_j), dk_j
+  double phiB, dkB;    // step whose second half is applied
+  double dz;
+  float kh[3];         // kappa_f * dz/2, including the 1/2 SH factor for 2 fields
+  float scale;         // output scale for XM_INV
+};
+
+struct AxisArgs {
+  float2* data;
+  int nx, ny, nt;
+  long long fstride;
+  long long ntiles;
+  int xtiles;
+  const float2* tw;    // twiddles of the transformed axis
+  const float2* px;    // [nf][nx] propagator factors (t-pass only)
+  const float2* py;    // [nf][ny]
+  const float2* pt;    // [nf][nt]
+  float scale;         // 1/(nx ny nt), folded into the multiplier
+};
+
+// ------------------------------------------------------------ tile shapes
+template <int N>
+__host__ __device__ constexpr int fft_threads() { return N / FftPlan<N>::E; }
+
+template <int N>
+__host__ __device__ constexpr int xpass_rows() {
+  return fft_threads<N>() >= 256 ? 1 : 256 / fft_threads<N>();
+}
+template <int N>
+__host__ __device__ constexpr int xpass_smem_floats2(int nf) {
+  return N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N);
+}
+
+// columns per tile for strided pencils: 128-byte rows up to N = 1024
+template <int N>
+__host__ __device__ constexpr int col_tile() { return N <= 1024 ? 16 : (N <= 2048 ? 8 : 4); }
+template <int N>
+__host__ __device__ constexpr int tiles_per_cta() {
+  return fft_threads<N>() * col_tile<N>() >= 256 ? 1 : 256 / (fft_threads<N>() * col_tile<N>());
+}
+template <int N>
+__host__ __device__ constexpr int axis_smem_floats2() {
+  return N + tiles_per_cta<N>() * N * col_tile<N>();
+}
+
+// -------------------------------------------------------- nonlinear step
+// Right-hand sides of Eqs. CEp/CEs/CEi (3 fields p, s, i) or of the
+// degenerate SHG pair (SH, F), already multiplied by the step h:
+//   c[f] = i kappa_f h e^{-/+ i Phi(z)}  (minus for field 0)
+template <int F>
+__device__ __forceinline__ void nl_rhs(const float2 (&a)[F], const float2* __restrict__ c,
+                                       float2 (&k)[F]) {
+  if constexpr (F == 3) {
+    k[0] = cmul(c[0], cmul(a[1], a[2]));
+    k[1] = cmul(c[1], cmulc(a[0], a[2]));
+    k[2] = cmul(c[2], cmulc(a[0], a[1]));
+  } else {
+    k[0] = cmul(c[0], cmul(a[1], a[1]));
+    k[1] = cmul(c[1], cmulc(a[0], a[1]));
+  }
+}
+
+// Classical RK4 over one half step; cs holds the coefficient sets at the
+// start, the midpoint and the end of the interval ([3][F]).
+template <int F>
+__device__ __forceinline__ void rk4(float2 (&a)[F], const float2* __restrict__ cs) {
+  float2 k[F], acc[F], t[F];
+  nl_rhs<F>(a, cs, k);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    acc[f] = k[f];
+    t[f] = make_float2(fmaf(0.5f, k[f].x, a[f].x), fmaf(0.5f, k[f].y, a[f].y));
+  }
+  nl_rhs<F>(t, cs + F, k);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    acc[f] = make_float2(fmaf(2.f, k[f].x, acc[f].x), fmaf(2.f, k[f].y, acc[f].y));
+    t[f] = make_float2(fmaf(0.5f, k[f].x, a[f].x), fmaf(0.5f, k[f].y, a[f].y));
+  }
+  nl_rhs<F>(t, cs + F, k);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    acc[f] = make_float2(fmaf(2.f, k[f].x, acc[f].x), fmaf(2.f, k[f].y, acc[f].y));
+    t[f] = cadd(a[f], k[f]);
+  }
+  nl_rhs<F>(t, cs + 2 * F, k);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    acc[f] = cadd(acc[f], k[f]);
+    a[f] = make_float2(fmaf(1.f / 6.f, acc[f].x, a[f].x), fmaf(1.f / 6.f, acc[f].y, a[f].y));
+  }
+}
+
+// e^{-i Phi} with Phi in FP64, reduced to [-pi, pi] before the FP32 sincos.
+__device__ __forceinline__ float2 phase_minus(double phi) {
+  const double two_pi = 6.283185307179586476925286766559;
+  double r = phi - two_pi * rint(phi / two_pi);
+  float s, c;
+  sincosf((float)r, &s, &c);
+  return make_float2(c, -s);
+}
+
+// Stage coefficients: sets 0..2 = second half of step B at z_B + dz/2,
+// z_B + 3dz/4, z_B + dz; sets 3..5 = first half of step A at z_A, z_A + dz/4,
+// z_A + dz/2.
+template <int F>
+__device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef) {
+  const int s = threadIdx.x;
+  if (s < 6) {
+    double phi;
+    if (s < 3) phi = p.phiB + p.dkB * (0.5 * p.dz + 0.25 * p.dz * s);
+    else phi = p.phiA + p.dkA * (0.25 * p.dz * (s - 3));
+    const float2 em = phase_minus(phi);  // e^{-i Phi}
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      // i * kh * e^{-i Phi} = kh (sin, cos) ; i * kh * e^{+i Phi} = kh (-sin, cos)
+      const float kh = p.kh[f];
+      coef[s * F + f] = f == 0 ? make_float2(-em.y * kh, em.x * kh) : make_float2(em.y * kh, em.x * kh);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ x-pass
+template <int NX, int F>
+__global__ void __launch_bounds__(xpass_rows<NX>() * fft_threads<NX>())
+    xpass_kernel(const XPassArgs p) {
+  constexpr int E = FftPlan<NX>::E;
+  constexpr int T = fft_threads<NX>();
+  constexpr int ROWS = xpass_rows<NX>();
+  constexpr int PITCH = XchRow::pitch(NX);
+  constexpr int RF0 = fft_radix<NX, false>(0);               // forward first radix
+  constexpr int RFL = fft_radix<NX, false>(FftPlan<NX>::NP - 1);  // forward last radix
+  constexpr int SF0 = NX / RF0, SFL = NX / RFL;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* coef = tw + NX;
+  float2* xch = coef + 6 * F;
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
+  nl_coefficients<F>(p, coef);
+  __syncthreads();
+
+  const int t = threadIdx.x % T;
+  const int rl = threadIdx.x / T;
+  const long long row = (long long)blockIdx.x * ROWS + rl;
+  const bool act = row < p.rows;
+  const XchRow xr{xch + rl * PITCH};
+  const int mode = p.mode;
+  const bool from_k = (mode == XM_INV || mode == XM_NL_MID || mode == XM_NL_LAST);
+
+  float2 v[F][E];
+  // The inverse transform's first pass reads positions t + b T + r NX/RFL and
+  // ends at t + b T + r NX/RF0, which are the forward transform's first-pass
+  // positions: registers flow from one to the other without an exchange.
+  if (from_k) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+#pragma unroll
+      for (int b = 0; b < E / RFL; ++b)
+#pragma unroll
+        for (int r = 0; r < RFL; ++r)
+          v[f][b * RFL + r] = act ? src[t + b * T + r * SFL] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f) fft_run<NX, true, 0>(v[f], t, xr, tw);
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+#pragma unroll
+      for (int b = 0; b < E / RF0; ++b)
+#pragma unroll
+        for (int r = 0; r < RF0; ++r)
+          v[f][b * RF0 + r] = act ? src[t + b * T + r * SF0] : make_float2(0.f, 0.f);
+    }
+  }
+
+  if (mode == XM_NL_MID || mode == XM_NL_LAST || mode == XM_NL_FIRST) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      float2 a[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) a[f] = v[f][e];
+      if (mode != XM_NL_FIRST) rk4<F>(a, coef);
+      if (mode != XM_NL_LAST) rk4<F>(a, coef + 3 * F);
+#pragma unroll
+      for (int f = 0; f < F; ++f) v[f][e] = a[f];
+    }
+  }
+
+  if (mode == XM_INV || mode == XM_NL_LAST) {
+    const float sc = mode == XM_INV ? p.scale : 1.f;
+    if (act) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        float2* dst = p.data + f * p.fstride + row * NX;
+#pragma unroll
+        for (int b = 0; b < E / RF0; ++b)
+#pragma unroll
+          for (int r = 0; r < RF0; ++r) dst[t + b * T + r * SF0] = cscale(v[f][b * RF0 + r], sc);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < F; ++f) fft_run<NX, false, 0>(v[f], t, xr, tw);
+    if (act) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        float2* dst = p.data + f * p.fstride + row * NX;
+#pragma unroll
+        for (int b = 0; b < E / RFL; ++b)
+#pragma unroll
+          for (int r = 0; r < RFL; ++r) dst[t + b * T + r * SFL] = v[f][b * RFL + r];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------- strided-axis passes
+// AXIS 1: pencils along y (stride nx), tiles over (f, tau, x-tile).
+// AXIS 2: pencils along tau (stride nx ny), tiles over (f, y, x-tile).
+template <int N, int AXIS>
+struct AxisTile {
+  float2* base;  // element (x, pencil index 0)
+  long long stride;
+  int f, other, x;
+  bool act;
+  __device__ __forceinline__ AxisTile(const AxisArgs& p, long long tile, int tx) {
+    constexpr int TX = col_tile<N>();
+    const int xt = (int)(tile % p.xtiles);
+    const long long rest = tile / p.xtiles;
+    const int no = AXIS == 1 ? p.nt : p.ny;
+    other = (int)(rest % no);
+    f = (int)(rest / no);
+    x = xt * TX + tx;
+    act = tile < p.ntiles && x < p.nx;
+    stride = AXIS == 1 ? (long long)p.nx : (long long)p.nx * p.ny;
+    const long long off = AXIS == 1 ? (long long)other * p.nx * p.ny + x : (long long)other * p.nx + x;
+    base = p.data + (act ? (long long)f * p.fstride + off : 0);
+  }
+};
+
+template <int N, bool INV, int AXIS>
+__global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_tile<N>())
+    axis_fft_kernel(const AxisArgs p) {
+  constexpr int E = FftPlan<N>::E, T = fft_threads<N>(), TX = col_tile<N>();
+  constexpr int TPC = tiles_per_cta<N>();
+  constexpr int R0 = fft_radix<N, INV>(0), RL = fft_radix<N, INV>(FftPlan<N>::NP - 1);
+  constexpr int S0 = N / R0, SL = N / RL;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* xch = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
+  __syncthreads();
+  const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
+  const int tx = lt % TX, t = lt / TX;
+  const AxisTile<N, AXIS> a(p, (long long)blockIdx.x * TPC + tl, tx);
+  const XchCol<TX> xc{xch + tl * N * TX, tx};
+  float2 v[E];
+#pragma unroll
+  for (int b = 0; b < E / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r)
+      v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
+  fft_run<N, INV, 0>(v, t, xc, tw);
+  if (a.act) {
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) a.base[(t + b * T + r * SL) * a.stride] = v[b * RL + r];
+  }
+}
+
+// Forward tau-FFT, propagator multiply, inverse tau-FFT, in one pass.
+template <int N>
+__global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_tile<N>())
+    tpass_prop_kernel(const AxisArgs p) {
+  constexpr int E = FftPlan<N>::E, T = fft_threads<N>(), TX = col_tile<N>();
+  constexpr int TPC = tiles_per_cta<N>();
+  constexpr int R0 = fft_radix<N, false>(0), RL = fft_radix<N, false>(FftPlan<N>::NP - 1);
+  constexpr int S0 = N / R0, SL = N / RL;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* xch = tw + N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
+  __syncthreads();
+  const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
+  const int tx = lt % TX, t = lt / TX;
+  const AxisTile<N, 2> a(p, (long long)blockIdx.x * TPC + tl, tx);
+  const XchCol<TX> xc{xch + tl * N * TX, tx};
+  float2 v[E];
+#pragma unroll
+  for (int b = 0; b < E / R0; ++b)
+#pragma unroll
+    for (int r = 0; r < R0; ++r)
+      v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
+  fft_run<N, false, 0>(v, t, xc, tw);
+  // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL
+  float2 pxy = make_float2(0.f, 0.f);
+  if (a.act) pxy = cscale(cmul(p.px[a.f * p.nx + a.x], p.py[a.f * p.ny + a.other]), p.scale);
+  const float2* pt = p.pt + (a.act ? a.f * p.nt : 0);
+#pragma unroll
+  for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+    for (int r = 0; r < RL; ++r) {
+      const int k = t + b * T + r * SL;
+      v[b * RL + r] = cmul(v[b * RL + r], cmul(pxy, pt[k]));
+    }
+  // the inverse's first pass reads exactly these positions
+  fft_run<N, true, 0>(v, t, xc, tw);
+  if (a.act) {
+#pragma unroll
+    for (int b = 0; b < E / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) a.base[(t + b * T + r * S0) * a.stride] = v[b * R0 + r];
+  }
+}
+
+// ------------------------------------------------------------ dispatchers
+// Each returns cudaErrorInvalidValue for an unsupported length.
+cudaError_t run_xpass(int nx, int nf, const XPassArgs& a, cudaStream_t s);
+cudaError_t run_axis_fft(int n, int axis, bool inv, const AxisArgs& a, cudaStream_t s);
+cudaError_t run_tpass_prop(int nt, const AxisArgs& a, cudaStream_t s);
+bool size_supported(int n);
+int col_tile_of(int n);
+
+// misc kernels (k_misc.cu)
+cudaError_t run_twiddles(float2* tw, int n, cudaStream_t s);
+struct TableArgs {
+  float2* px;
+  float2* py;
+  float2* pt;
+  int nx, ny, nt, nf;
+  double dx, dy, dt, dz;
+  double k[3], rho[3], delta[3], k2[3], k3[3], alpha[3];
+};
+cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s);
+cudaError_t run_energy(const float2* data, long long n, int nf, long long fstride, double* partial,
+                       int nblocks, double* out, cudaStream_t s);
+cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
+cudaError_t run_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t s);
+
+}  // namespace brahms
+
+// Supported transform lengths (each needs an FftPlan).
+#define BRAHMS_FOR_EACH_SIZE(X) \
+  X(2) X(4) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048) X(4096) \
+  X(6) X(12) X(24) X(48) X(96) X(192) X(384) X(768)

@@ -1,0 +1,281 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Tolerances: fields within 1e-4 relative L2 per field (FP32 bulk arithmetic
+against FP64), energies within 1e-5 relative.  Single transforms are held to
+1e-5 (an FP32 FFT's rounding error grows like sqrt(log N) ulp)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_08384_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-4
+ENERGY_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_08384_gb300 import build
+    build.build()
+
+
+def _br():
+    import paper_2609_08384_gb300 as br
+    return br
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.complex64)
+
+
+def _dev(arrs):
+    return [torch.from_numpy(_c64(a)).cuda() for a in arrs]
+
+
+def _smooth(grid, rng, amp, width=0.12):
+    shape = (grid.nt, grid.ny, grid.nx)
+    spec = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    kt = np.fft.fftfreq(grid.nt)[:, None, None]
+    ky = np.fft.fftfreq(grid.ny)[None, :, None]
+    kx = np.fft.fftfreq(grid.nx)[None, None, :]
+    spec *= np.exp(-(kt**2 + ky**2 + kx**2) / (2 * width**2))
+    f = np.fft.ifftn(spec)
+    return amp * f / np.abs(f).max()
+
+
+def _opg_fields(alpha=0.0, k3=0.0):
+    return [wl.FieldParams(wl.LAM_P, wl.N_P, delta=1e-10, k2=2e-25, k3=k3, rho=2e-3, alpha=alpha),
+            wl.FieldParams(wl.LAM_S, wl.N_S, k2=1e-25, k3=-k3),
+            wl.FieldParams(wl.LAM_I, wl.N_I, delta=-1e-10, k2=5e-26, rho=1e-3, alpha=2 * alpha)]
+
+
+SIZES = [2, 4, 8, 16, 32, 64, 128, 256, 512, 1024, 2048, 4096, 6, 12, 24, 48, 96, 192, 384, 768]
+SHAPES = sorted({s for n in SIZES for s in [(n, 4, 6), (6, n, 4), (4, 6, n)]} |
+                {(96, 64, 128), (24, 48, 96), (256, 32, 512), (48, 192, 12)})
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_transform_matches_oracle_fft(shape):
+    br = _br()
+    nx, ny, nt = shape
+    g = wl.Grid(nx, ny, nt, 1e-6, 1e-6, 1e-14)
+    rng = np.random.default_rng(nx * 7 + ny * 13 + nt)
+    init = [_c64(rng.standard_normal((nt, ny, nx)) + 1j * rng.standard_normal((nt, ny, nx))) for _ in range(2)]
+    s = br.Solver(g, wl.shg_fields(), wl.D_EFF, 0.0)
+    s.set_fields(_dev(init))
+    s.transform(-1)
+    got = s.get_fields()
+    for f in range(2):
+        ref = oracle.fft3(init[f].astype(np.complex128), -1)
+        assert rel_l2(got[f], ref) < 1e-5, (shape, f)
+    s.transform(+1)
+    back = s.get_fields()
+    for f in range(2):
+        assert rel_l2(back[f], init[f]) < 1e-5
+    s.close()
+
+
+def _run_both(grid, fields, init, nz, dz, dk, d_eff=wl.D_EFF, profile=None):
+    br = _br()
+    s = br.Solver(grid, fields, d_eff, dk)
+    s.set_fields(_dev(init))
+    dks = np.full(nz, dk)
+    if profile is not None:
+        s.set_dk_profile(profile)
+        dks[:len(profile)] = profile[:nz]
+    s.propagate(nz, dz)
+    got = s.get_fields()
+    e_gpu, _ = s.energy()
+    z, phi = s.get_z()
+    s.close()
+    prob = oracle.make_problem(grid, fields, d_eff)
+    ref, phi_ref = oracle.propagate(prob, [a.astype(np.complex128) for a in map(_c64, init)], nz, dz, dks)
+    e_ref, _ = oracle.energy(prob, ref)
+    assert abs(z - nz * dz) < 1e-15 and abs(phi - phi_ref) < 1e-9 * max(1.0, abs(phi_ref))
+    return got, ref, e_gpu, e_ref
+
+
+def test_shg_32x32x64_100_steps():
+    """SHG, 2 complex fields (SH, F) on 32x32x64, 100 steps of 10 um over 1 mm,
+    1 GW/cm^2 focused 200 fs pulse at 1064 nm, strong depletion."""
+    p = wl.problem_shg_small()
+    init = wl.inputs_shg_small(p)
+    got, ref, e_gpu, e_ref = _run_both(p.grid, p.fields, init, p.nz, p.dz, p.dk)
+    for f in range(2):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL, f
+        assert abs(e_gpu[f] / e_ref[f] - 1) < ENERGY_TOL
+    # conversion actually happened (eta of order 0.1 and more)
+    assert e_ref[0] > 0.05 * (e_ref[0] + e_ref[1])
+
+
+@pytest.mark.parametrize("shape", [(24, 48, 96), (48, 24, 12), (96, 6, 64)])
+def test_three_fields_all_terms_ragged(shape):
+    """3 fields with walk-off, GVM, GVD, TOD, loss and mismatch on grids whose
+    x extent leaves a ragged column tile."""
+    nx, ny, nt = shape
+    g = wl.Grid(nx, ny, nt, 4 * wl.UM, 4 * wl.UM, 30 * wl.FS)
+    fields = _opg_fields(alpha=30.0, k3=4e-40)
+    rng = np.random.default_rng(sum(shape))
+    init = [_smooth(g, rng, 5e7) for _ in range(3)]
+    got, ref, e_gpu, e_ref = _run_both(g, fields, init, 20, 8 * wl.UM, 700.0)
+    for f in range(3):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL, f
+        assert abs(e_gpu[f] / e_ref[f] - 1) < ENERGY_TOL
+
+
+def test_shg_dk_profile():
+    """Piecewise Delta k_j per step (shorter than nz: the constant applies after it)."""
+    g = wl.Grid(32, 32, 64, 12.5 * wl.UM, 12.5 * wl.UM, 50 * wl.FS)
+    p = wl.problem_shg_small()
+    init = wl.inputs_shg_small(p)
+    rng = np.random.default_rng(77)
+    prof = rng.normal(0, 0.1, 30) / wl.MM
+    got, ref, _, _ = _run_both(g, p.fields, init, 40, 10 * wl.UM, 55.0, profile=prof)
+    for f in range(2):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL
+
+
+def test_resume_is_bit_identical():
+    """Two calls of 7 and 9 steps equal one call of 16 (the peeled x-pass
+    performs the same FP32 operations as the fused one)."""
+    br = _br()
+    g = wl.Grid(32, 16, 64, 5 * wl.UM, 5 * wl.UM, 30 * wl.FS)
+    fields = _opg_fields()
+    rng = np.random.default_rng(5)
+    init = _dev([_smooth(g, rng, 4e7) for _ in range(3)])
+    a = br.Solver(g, fields, wl.D_EFF, 123.0)
+    a.set_fields(init)
+    a.propagate(7, 6 * wl.UM)
+    a.propagate(9, 6 * wl.UM)
+    ga = a.get_fields()
+    b = br.Solver(g, fields, wl.D_EFF, 123.0)
+    b.set_fields(init)
+    b.propagate(16, 6 * wl.UM)
+    gb = b.get_fields()
+    for f in range(3):
+        assert np.array_equal(ga[f], gb[f])
+    a.close()
+    b.close()
+
+
+def test_deterministic_repeat():
+    br = _br()
+    p = wl.problem_shg_small()
+    init = _dev(wl.inputs_shg_small(p))
+    outs = []
+    for _ in range(2):
+        s = br.Solver(p.grid, p.fields, p.d_eff, 40.0)
+        s.set_fields(init)
+        s.propagate(30, p.dz)
+        outs.append(s.get_fields())
+        s.close()
+    for f in range(2):
+        assert np.array_equal(outs[0][f], outs[1][f])
+
+
+def test_sfg_128x128x256_six_steps():
+    """SFG configuration at full size (3 x 128x128x256), first 6 of its 500 steps."""
+    p = wl.problem_sfg()
+    init = wl.inputs_sfg(p)
+    got, ref, e_gpu, e_ref = _run_both(p.grid, p.fields, init, 6, p.dz, p.dk)
+    for f in (1, 2):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL, f
+    # the generated pump starts at zero; compare it against the total field scale
+    assert np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[1]) < FIELD_TOL
+    assert rel_l2(got[0], ref[0]) < 1e-3
+    for f in range(3):
+        assert abs(e_gpu[f] / e_ref[f] - 1) < (ENERGY_TOL if f else 1e-3)
+
+
+def test_opg_256x256x512_two_steps_full_size():
+    """OPG configuration at full size (3 x 256x256x512) in the launch shapes the
+    benchmark times: two split steps against the oracle."""
+    p = wl.problem_opg()
+    init = wl.inputs_opg(p)
+    got, ref, e_gpu, e_ref = _run_both(p.grid, p.fields, init, 2, p.dz, p.dk)
+    for f in range(3):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL, f
+        assert abs(e_gpu[f] / e_ref[f] - 1) < ENERGY_TOL
+
+
+def test_opg_full_size_invariants_300_steps():
+    """Lossless OPG at full size: total energy sum n|A|^2 and the Manley-Rowe
+    signal-minus-idler photon number are conserved along z (any size)."""
+    br = _br()
+    p = wl.problem_opg()
+    init = wl.inputs_opg(p)
+    s = br.Solver(p.grid, p.fields, p.d_eff, p.dk)
+    s.set_fields(_dev(init))
+    e0, n0 = s.energy()
+    s.propagate(300, p.dz)
+    e1, n1 = s.energy()
+    s.close()
+    assert abs(e1.sum() / e0.sum() - 1) < ENERGY_TOL
+    assert abs((n1[1] - n1[2]) - (n0[1] - n0[2])) / n0.sum() < ENERGY_TOL
+    assert abs((n1[0] + n1[1]) / (n0[0] + n0[1]) - 1) < ENERGY_TOL
+    assert n1[1] > 10 * n0[1]  # parametric gain happened
+
+
+def test_status_codes():
+    br = _br()
+    g = wl.Grid(32, 32, 64, 12.5 * wl.UM, 12.5 * wl.UM, 50 * wl.FS)
+    with pytest.raises(br.BrahmsError) as ei:
+        br.Solver(wl.Grid(40, 32, 64, 1e-6, 1e-6, 1e-14), wl.shg_fields(), wl.D_EFF, 0.0)
+    assert ei.value.status == br.BRAHMS_E_SIZE
+    s = br.Solver(g, wl.shg_fields(), wl.D_EFF, 0.0)
+    with pytest.raises(br.BrahmsError) as ei:
+        s.propagate(3, 1e-6)
+    assert ei.value.status == br.BRAHMS_E_STATE
+    bad = np.zeros((64, 32, 32), np.complex64)
+    bad[3, 4, 5] = np.nan
+    with pytest.raises(br.BrahmsError) as ei:
+        s.set_fields([torch.from_numpy(bad).cuda(), torch.zeros(64, 32, 32, dtype=torch.complex64).cuda()])
+    assert ei.value.status == br.BRAHMS_E_ARG
+    big = np.full((64, 32, 32), 1e12, np.complex64)
+    s.set_fields([torch.zeros(64, 32, 32, dtype=torch.complex64).cuda(), torch.from_numpy(big).cuda()])
+    with pytest.raises(br.BrahmsError) as ei:
+        s.propagate(-1, 1e-6)
+    assert ei.value.status == br.BRAHMS_E_ARG
+    s.propagate(20, 1.0)  # |Delta A| >> |A|: blows up (Sec. 3.2)
+    with pytest.raises(br.BrahmsError) as ei:
+        s.energy()
+    assert ei.value.status == br.BRAHMS_E_NONFINITE
+    s.close()
+
+
+def test_host_and_c128_paths_match_device_c64():
+    br = _br()
+    p = wl.problem_shg_small()
+    init = wl.inputs_shg_small(p)
+    outs = []
+    for mode in ("dev64", "host64", "host128", "dev128"):
+        s = br.Solver(p.grid, p.fields, p.d_eff, 0.0)
+        if mode == "dev64":
+            s.set_fields(_dev(init))
+        elif mode == "host64":
+            s.set_fields([_c64(a) for a in init])
+        elif mode == "host128":
+            s.set_fields([np.ascontiguousarray(_c64(a).astype(np.complex128)) for a in init])
+        else:
+            s.set_fields([torch.from_numpy(_c64(a).astype(np.complex128)).cuda() for a in init])
+        s.propagate(5, p.dz)
+        if mode == "dev128":
+            o = s.get_fields(dtype=np.complex128, on_device=True)
+            outs.append([x.cpu().numpy().astype(np.complex64) for x in o])
+        else:
+            outs.append(s.get_fields(dtype=np.complex128 if mode == "host128" else np.complex64))
+        s.close()
+    for o in outs[1:]:
+        for f in range(2):
+            assert np.array_equal(np.asarray(o[f]).astype(np.complex64), outs[0][f])
