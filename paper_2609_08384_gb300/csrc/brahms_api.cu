@@ -37,9 +37,9 @@ Layout make_layout(int nx, int ny, int nt, int nf) {
   L.px = take(sizeof(float2) * nx * nf);
   L.py = take(sizeof(float2) * ny * nf);
   L.pt = take(sizeof(float2) * nt * nf);
-  L.twx = take(sizeof(float2) * nx);
-  L.twy = take(sizeof(float2) * ny);
-  L.twt = take(sizeof(float2) * nt);
+  L.twx = take(sizeof(float4) * nx);
+  L.twy = take(sizeof(float4) * ny);
+  L.twt = take(sizeof(float4) * nt);
   L.partial = take(sizeof(double) * kRedBlocks * nf);
   L.energy = take(sizeof(double) * nf);
   L.total = off;
@@ -62,7 +62,7 @@ struct brahms_ctx {
   char* ws = nullptr;
   Layout L{};
   float2 *state = nullptr, *px = nullptr, *py = nullptr, *pt = nullptr;
-  float2 *twx = nullptr, *twy = nullptr, *twt = nullptr;
+  float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
   double *partial = nullptr, *energy_dev = nullptr;
   double* energy_host = nullptr;  // pinned, nf entries
   double tab_dz = NAN;
@@ -213,7 +213,9 @@ brahms::AxisArgs aargs(brahms_ctx* c, int axis) {
   a.px = c->px;
   a.py = c->py;
   a.pt = c->pt;
-  a.scale = (float)(1.0 / (double)c->npoints());
+  const double inv_n = 1.0 / (double)c->npoints();
+  a.scale = (float)inv_n;
+  a.scale_lo = (float)(inv_n - (double)a.scale);
   return a;
 }
 
@@ -326,9 +328,9 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->px = (float2*)(ctx->ws + ctx->L.px);
   ctx->py = (float2*)(ctx->ws + ctx->L.py);
   ctx->pt = (float2*)(ctx->ws + ctx->L.pt);
-  ctx->twx = (float2*)(ctx->ws + ctx->L.twx);
-  ctx->twy = (float2*)(ctx->ws + ctx->L.twy);
-  ctx->twt = (float2*)(ctx->ws + ctx->L.twt);
+  ctx->twx = (float4*)(ctx->ws + ctx->L.twx);
+  ctx->twy = (float4*)(ctx->ws + ctx->L.twy);
+  ctx->twt = (float4*)(ctx->ws + ctx->L.twt);
   ctx->partial = (double*)(ctx->ws + ctx->L.partial);
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
   cudaError_t e = cudaSuccess;

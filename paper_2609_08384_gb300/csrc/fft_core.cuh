@@ -36,17 +36,44 @@ template <bool INV>
 __device__ __forceinline__ float2 rot90(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
-// multiply by the constant W = cos(theta) -/+ i sin(theta) (forward uses minus)
-template <bool INV>
-__device__ __forceinline__ float2 twc(float2 a, float c, float s) {
-  return INV ? make_float2(fmaf(a.x, c, -a.y * s), fmaf(a.y, c, a.x * s))
-             : make_float2(fmaf(a.x, c, a.y * s), fmaf(a.y, c, -a.x * s));
-}
+// Irrational codelet constants as hi + lo float pairs.  Rounded to one float
+// each, cos(pi/4), cos(pi/8) and sin(pi/8) all have |w| slightly below 1
+// (|w|^2 - 1 = -3.4e-8 for the pi/4 pair, -5.7e-8 for the pi/8 pair), and
+// because a z-step applies the same factors again and again the field energy
+// would drift by about -2e-7 per step.  Multiplying by hi and lo (one extra
+// FMA) makes each product correctly rounded, so rounding errors are unbiased.
+constexpr double kS2d = 0.70710678118654752440084436210485;   // cos(pi/4)
+constexpr double kC16d = 0.92387953251128675612818318939679;  // cos(pi/8)
+constexpr double kS16d = 0.38268343236508977172845998403040;  // sin(pi/8)
+constexpr double kS3d = 0.86602540378443864676372317075294;   // sin(pi/3)
+constexpr float kS2 = (float)kS2d, kS2lo = (float)(kS2d - (double)(float)kS2d);
+constexpr float kC16 = (float)kC16d, kC16lo = (float)(kC16d - (double)(float)kC16d);
+constexpr float kS16 = (float)kS16d, kS16lo = (float)(kS16d - (double)(float)kS16d);
+constexpr float kS3 = (float)kS3d, kS3lo = (float)(kS3d - (double)(float)kS3d);
 
-constexpr float kS2 = 0.70710678118654752440f;   // cos(pi/4)
-constexpr float kC16 = 0.92387953251128675613f;  // cos(pi/8)
-constexpr float kS16 = 0.38268343236508977173f;  // sin(pi/8)
-constexpr float kS3 = 0.86602540378443864676f;   // sin(pi/3)
+// u * c with c = hi + lo
+__device__ __forceinline__ float xmul(float u, float hi, float lo) { return fmaf(u, hi, u * lo); }
+// a * (c -/+ i s) with c = ch + cl, s = sh + sl (forward uses minus)
+template <bool INV>
+__device__ __forceinline__ float2 twx(float2 a, float ch, float cl, float sh, float sl) {
+  if (INV)
+    return make_float2(fmaf(a.x, ch, fmaf(-a.y, sh, fmaf(a.x, cl, -a.y * sl))),
+                       fmaf(a.y, ch, fmaf(a.x, sh, fmaf(a.y, cl, a.x * sl))));
+  return make_float2(fmaf(a.x, ch, fmaf(a.y, sh, fmaf(a.x, cl, a.y * sl))),
+                     fmaf(a.y, ch, fmaf(-a.x, sh, fmaf(a.y, cl, -a.x * sl))));
+}
+// a * W8^1 (forward: (1 - i)/sqrt 2; inverse: (1 + i)/sqrt 2)
+template <bool INV>
+__device__ __forceinline__ float2 w8_1(float2 a) {
+  return INV ? make_float2(xmul(a.x - a.y, kS2, kS2lo), xmul(a.x + a.y, kS2, kS2lo))
+             : make_float2(xmul(a.x + a.y, kS2, kS2lo), xmul(a.y - a.x, kS2, kS2lo));
+}
+// a * W8^3 (forward: (-1 - i)/sqrt 2; inverse: (-1 + i)/sqrt 2)
+template <bool INV>
+__device__ __forceinline__ float2 w8_3(float2 a) {
+  return INV ? make_float2(-xmul(a.x + a.y, kS2, kS2lo), xmul(a.x - a.y, kS2, kS2lo))
+             : make_float2(xmul(a.y - a.x, kS2, kS2lo), -xmul(a.x + a.y, kS2, kS2lo));
+}
 
 // ---------------------------------------------------------------- codelets
 template <bool INV>
@@ -69,7 +96,8 @@ template <bool INV>
 __device__ __forceinline__ void dft3(float2& v0, float2& v1, float2& v2) {
   float2 s = cadd(v1, v2);
   float2 t = make_float2(fmaf(-0.5f, s.x, v0.x), fmaf(-0.5f, s.y, v0.y));
-  float2 u = rot90<INV>(cscale(csub(v1, v2), kS3));
+  const float2 d = csub(v1, v2);
+  float2 u = rot90<INV>(make_float2(xmul(d.x, kS3, kS3lo), xmul(d.y, kS3, kS3lo)));
   v0 = cadd(v0, s);
   v1 = cadd(t, u);
   v2 = csub(t, u);
@@ -84,9 +112,9 @@ __device__ __forceinline__ void dft8(float2* v) {
     y0[n2] = cadd(v[n2], v[n2 + 4]);
     y1[n2] = csub(v[n2], v[n2 + 4]);
   }
-  y1[1] = twc<INV>(y1[1], kS2, kS2);
+  y1[1] = w8_1<INV>(y1[1]);
   y1[2] = rot90<INV>(y1[2]);
-  y1[3] = twc<INV>(y1[3], -kS2, kS2);
+  y1[3] = w8_3<INV>(y1[3]);
   dft4<INV>(y0[0], y0[1], y0[2], y0[3]);
   dft4<INV>(y1[0], y1[1], y1[2], y1[3]);
 #pragma unroll
@@ -100,12 +128,12 @@ __device__ __forceinline__ void dft8(float2* v) {
 template <bool INV, int E>
 __device__ __forceinline__ float2 w16(float2 a) {
   if constexpr (E == 0) return a;
-  else if constexpr (E == 1) return twc<INV>(a, kC16, kS16);
-  else if constexpr (E == 2) return twc<INV>(a, kS2, kS2);
-  else if constexpr (E == 3) return twc<INV>(a, kS16, kC16);
+  else if constexpr (E == 1) return twx<INV>(a, kC16, kC16lo, kS16, kS16lo);
+  else if constexpr (E == 2) return w8_1<INV>(a);
+  else if constexpr (E == 3) return twx<INV>(a, kS16, kS16lo, kC16, kC16lo);
   else if constexpr (E == 4) return rot90<INV>(a);
-  else if constexpr (E == 6) return twc<INV>(a, -kS2, kS2);
-  else if constexpr (E == 9) return twc<INV>(a, -kC16, -kS16);
+  else if constexpr (E == 6) return w8_3<INV>(a);
+  else if constexpr (E == 9) return twx<INV>(a, -kC16, -kC16lo, -kS16, -kS16lo);
   else return a;
 }
 
@@ -224,9 +252,15 @@ struct XchCol {
 
 // Passes P..NP-1 of a length-N transform on the registers v (see header).
 // Every thread of the CTA must call this (it contains __syncthreads()).
+// Twiddle tables hold W_N^k = (c, s) as hi + lo float pairs, float4 (ch, sh,
+// cl, sl): a product with the table is then correctly rounded, so the FFT
+// carries no systematic modulus error from rounded twiddles.
+__device__ __forceinline__ float2 tw_mul(float2 a, float4 w) { return twx<true>(a, w.x, w.z, w.y, w.w); }
+__device__ __forceinline__ float2 tw_mulc(float2 a, float4 w) { return twx<false>(a, w.x, w.z, w.y, w.w); }
+
 template <int N, bool INV, int P, class X>
 __device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const X& x,
-                                        const float2* __restrict__ tw) {
+                                        const float4* __restrict__ tw) {
   constexpr int NP = FftPlan<N>::NP;
   constexpr int E = FftPlan<N>::E;
   constexpr int T = N / E;
@@ -241,8 +275,8 @@ __device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const
       const int m = j % NS;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float2 w = tw[r * m * (N / (NS * R))];
-        v[b * R + r] = INV ? cmulc(v[b * R + r], w) : cmul(v[b * R + r], w);
+        const float4 w = tw[r * m * (N / (NS * R))];
+        v[b * R + r] = INV ? tw_mulc(v[b * R + r], w) : tw_mul(v[b * R + r], w);
       }
     }
   }

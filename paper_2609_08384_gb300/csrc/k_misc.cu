@@ -3,17 +3,18 @@
 
 namespace brahms {
 
-// tw[k] = exp(-2 pi i k / n), evaluated in FP64 and rounded once to FP32.
-__global__ void twiddle_kernel(float2* tw, int n) {
+// tw[k] = exp(-2 pi i k / n) evaluated in FP64 and split into hi + lo floats.
+__global__ void twiddle_kernel(float4* tw, int n) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) {
     double s, c;
     sincospi(-2.0 * (double)k / (double)n, &s, &c);
-    tw[k] = make_float2((float)c, (float)s);
+    const float ch = (float)c, sh = (float)s;
+    tw[k] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
   }
 }
 
-cudaError_t run_twiddles(float2* tw, int n, cudaStream_t s) {
+cudaError_t run_twiddles(float4* tw, int n, cudaStream_t s) {
   twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
   return cudaPeekAtLastError();
 }
@@ -24,18 +25,25 @@ __device__ __forceinline__ double ang_freq(int m, int n, double d) {
   return 6.283185307179586476925286766559 * (double)mm / ((double)n * d);
 }
 
-// exp(i phi) with the FP64 phase reduced to [-pi, pi] before the FP32 sincos.
-__device__ __forceinline__ float2 unit_phase(double phi, double amp) {
+// amp * exp(i phi) - 1 ("delta form").  The phase argument is formed and
+// reduced to [-pi, pi] in FP64, then evaluated with FP32 sines:
+//   amp cos(phi) - 1 = (amp - 1) - 2 amp sin^2(phi/2),   amp sin(phi).
+// Stored this way, a factor with a small phase keeps |1 + D| = amp to FP32
+// relative precision of the small part, so repeated application does not
+// bias the field energy.
+__device__ __forceinline__ float2 delta_phase(double phi, double amp_m1) {
   const double two_pi = 6.283185307179586476925286766559;
   const double r = phi - two_pi * rint(phi / two_pi);
-  float s, c;
-  sincosf((float)r, &s, &c);
-  return make_float2((float)amp * c, (float)amp * s);
+  const float sh = sinf((float)(0.5 * r));
+  const float s = sinf((float)r);
+  const float am1 = (float)amp_m1;
+  const float amp = (float)(1.0 + amp_m1);
+  return make_float2(fmaf(-2.f * amp * sh, sh, am1), amp * s);
 }
 
 // Separable factors of the linear propagator over dz (Eqs. dispOp, diffOp,
 // with d/dx -> i kx, d/dtau -> i Omega, diffraction +(i/2k) Laplacian and the
-// unitary third-order term):
+// unitary third-order term), each stored as D = P - 1:
 //   Px = exp(-i dz [kx^2/(2k) + tan(rho) kx])
 //   Py = exp(-i dz ky^2/(2k))
 //   Pt = exp(dz [-alpha/2 - i delta Omega + i k2/2 Omega^2 - i k3/6 Omega^3])
@@ -48,19 +56,19 @@ __global__ void prop_tables_kernel(const TableArgs a) {
   if (m < a.nx) {
     const double kx = ang_freq(m, a.nx, a.dx);
     const double ph = -a.dz * (kx * kx / (2.0 * a.k[f]) + tan(a.rho[f]) * kx);
-    a.px[f * a.nx + m] = unit_phase(ph, 1.0);
+    a.px[f * a.nx + m] = delta_phase(ph, 0.0);
     return;
   }
   m -= a.nx;
   if (m < a.ny) {
     const double ky = ang_freq(m, a.ny, a.dy);
-    a.py[f * a.ny + m] = unit_phase(-a.dz * ky * ky / (2.0 * a.k[f]), 1.0);
+    a.py[f * a.ny + m] = delta_phase(-a.dz * ky * ky / (2.0 * a.k[f]), 0.0);
     return;
   }
   m -= a.ny;
   const double om = ang_freq(m, a.nt, a.dt);
   const double ph = a.dz * (-a.delta[f] * om + 0.5 * a.k2[f] * om * om - a.k3[f] / 6.0 * om * om * om);
-  a.pt[f * a.nt + m] = unit_phase(ph, exp(-0.5 * a.alpha[f] * a.dz));
+  a.pt[f * a.nt + m] = delta_phase(ph, expm1(-0.5 * a.alpha[f] * a.dz));
 }
 
 cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s) {

@@ -26,7 +26,7 @@ struct XPassArgs {
   float2* data;        // [nf][rows][nx]
   long long fstride;   // elements between fields
   long long rows;      // ny * nt
-  const float2* tw;    // e^{-2 pi i k / nx}, k < nx
+  const float4* tw;    // e^{-2 pi i k / nx}, k < nx, as hi/lo pairs
   int mode;            // XMode
   double phiA, dkA;    // step whose first half is applied: Phi(z_j), dk_j
   double phiB, dkB;    // step whose second half is applied
@@ -41,11 +41,11 @@ struct AxisArgs {
   long long fstride;
   long long ntiles;
   int xtiles;
-  const float2* tw;    // twiddles of the transformed axis
+  const float4* tw;    // twiddles of the transformed axis (hi/lo pairs)
   const float2* px;    // [nf][nx] propagator factors (t-pass only)
   const float2* py;    // [nf][ny]
   const float2* pt;    // [nf][nt]
-  float scale;         // 1/(nx ny nt), folded into the multiplier
+  float scale, scale_lo;  // 1/(nx ny nt) = scale + scale_lo (lo = 0 for powers of two)
 };
 
 // ------------------------------------------------------------ tile shapes
@@ -58,7 +58,7 @@ __host__ __device__ constexpr int xpass_rows() {
 }
 template <int N>
 __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
-  return N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N);
+  return 2 * N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N);
 }
 
 // columns per tile for strided pencils: 128-byte rows up to N = 1024
@@ -70,7 +70,7 @@ __host__ __device__ constexpr int tiles_per_cta() {
 }
 template <int N>
 __host__ __device__ constexpr int axis_smem_floats2() {
-  return N + tiles_per_cta<N>() * N * col_tile<N>();
+  return 2 * N + tiles_per_cta<N>() * N * col_tile<N>();
 }
 
 // -------------------------------------------------------- nonlinear step
@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(xpass_rows<NX>() * fft_threads<NX>())
   constexpr int RF0 = fft_radix<NX, false>(0);               // forward first radix
   constexpr int RFL = fft_radix<NX, false>(FftPlan<NX>::NP - 1);  // forward last radix
   constexpr int SF0 = NX / RF0, SFL = NX / RFL;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* coef = tw + NX;
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* coef = reinterpret_cast<float2*>(tw + NX);
   float2* xch = coef + 6 * F;
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
   nl_coefficients<F>(p, coef);
@@ -277,9 +277,9 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
   constexpr int TPC = tiles_per_cta<N>();
   constexpr int R0 = fft_radix<N, INV>(0), RL = fft_radix<N, INV>(FftPlan<N>::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* xch = tw + N;
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* xch = reinterpret_cast<float2*>(tw + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
   __syncthreads();
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
   constexpr int TPC = tiles_per_cta<N>();
   constexpr int R0 = fft_radix<N, false>(0), RL = fft_radix<N, false>(FftPlan<N>::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* xch = tw + N;
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* xch = reinterpret_cast<float2*>(tw + N);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
   __syncthreads();
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
@@ -325,16 +325,24 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
     for (int r = 0; r < R0; ++r)
       v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
   fft_run<N, false, 0>(v, t, xc, tw);
-  // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL
-  float2 pxy = make_float2(0.f, 0.f);
-  if (a.act) pxy = cscale(cmul(p.px[a.f * p.nx + a.x], p.py[a.f * p.ny + a.other]), p.scale);
+  // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL.
+  // P = (1 + Dx)(1 + Dy)(1 + Dt) applied as w + w D with w = v/(nx ny nt).
+  float2 dxy = make_float2(0.f, 0.f);
+  if (a.act) {
+    const float2 dx = p.px[a.f * p.nx + a.x], dy = p.py[a.f * p.ny + a.other];
+    dxy = cadd(cadd(dx, dy), cmul(dx, dy));
+  }
   const float2* pt = p.pt + (a.act ? a.f * p.nt : 0);
 #pragma unroll
   for (int b = 0; b < E / RL; ++b)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const int k = t + b * T + r * SL;
-      v[b * RL + r] = cmul(v[b * RL + r], cmul(pxy, pt[k]));
+      const float2 dt = pt[k];
+      const float2 d = cadd(cadd(dxy, dt), cmul(dxy, dt));
+      float2 w = v[b * RL + r];
+      w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
+      v[b * RL + r] = cadd(w, cmul(w, d));
     }
   // the inverse's first pass reads exactly these positions
   fft_run<N, true, 0>(v, t, xc, tw);
@@ -355,7 +363,7 @@ bool size_supported(int n);
 int col_tile_of(int n);
 
 // misc kernels (k_misc.cu)
-cudaError_t run_twiddles(float2* tw, int n, cudaStream_t s);
+cudaError_t run_twiddles(float4* tw, int n, cudaStream_t s);
 struct TableArgs {
   float2* px;
   float2* py;
