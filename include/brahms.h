@@ -126,6 +126,31 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
 /* Number of kernel launches this context has enqueued since creation. */
 long long brahms_launch_count(const brahms_ctx* ctx);
 
+/* Allocation-free energy of caller-owned device fields.  (The paper has no
+ * counterpart; this serves callers that cannot let the library allocate
+ * device memory: hosts whose GPU memory is all owned by another allocator,
+ * plugin environments that forbid a library's own cudaMalloc, and tight
+ * loops that cannot afford the device-wide synchronisation cudaMalloc and
+ * cudaFree may cause.)  Computes the same per-field energy as brahms_energy,
+ * E_f = 1/2 c eps0 n_f sum |A_f|^2 dx dy dtau [J], without a context and
+ * without allocating anything.
+ *   fields: nfields device pointers, each to nt*ny*nx complex64 [nt][ny][nx];
+ *   fp: nfields records (only n is used); energy_j_dev: device array of
+ *   nfields doubles, written on cuda_stream (NULL = legacy default stream).
+ * The partial sums live in one fixed 24 KiB device array inside the library
+ * (3 fields x 1024 partials), which every GPU that loads the library keeps
+ * until the process exits.  Limits: 1 <= nfields <= 3 and nx*ny*nt <= 2^40,
+ * else BRAHMS_E_SIZE.  Each call writes every partial it reads, so no state
+ * carries over, but all calls share that array: calls whose work overlaps on
+ * the GPU (other streams, other threads) race and must be serialised by the
+ * caller.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Returns E_ARG for NULL pointers or
+ * non-positive spacings, E_CUDA if a launch fails; asynchronous otherwise. */
+brahms_status brahms_energy_static(const void* const* fields, int nfields, int nx, int ny, int nt, double dx,
+                                   double dy, double dt, const brahms_field_params* fp, double* energy_j_dev,
+                                   void* cuda_stream);
+
 /* Release the context and any memory the library allocated for it. */
 void brahms_free(brahms_ctx* ctx);
 

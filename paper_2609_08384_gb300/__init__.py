@@ -58,6 +58,8 @@ SIGNATURES = {
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
     "brahms_launch_count": (_c.c_longlong, [_vp]),
+    "brahms_energy_static": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double,
+                                        _c.c_double, _c.c_double, _c.POINTER(FieldParams), _vp, _vp]),
     "brahms_free": (None, [_vp]),
     "brahms_last_error": (_c.c_char_p, [_vp]),
     "brahms_status_string": (_c.c_char_p, [_c.c_int]),
