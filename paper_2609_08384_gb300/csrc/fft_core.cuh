@@ -181,57 +181,56 @@ __device__ __forceinline__ void dft(float2* v) {
 }
 
 // ------------------------------------------------------------------- plans
-// Forward radix sequence and registers per thread (E, a multiple of every
-// radix) for each supported length.
+// A plan: length N, registers per thread E (a multiple of every radix), and
+// the forward radix sequence.  Kernels pick a plan per length.
+template <int N_, int E_, int NP_, int R0_, int R1_ = 0, int R2_ = 0, int R3_ = 0>
+struct Plan {
+  static constexpr int N = N_;
+  static constexpr int E = E_;
+  static constexpr int NP = NP_;
+  static constexpr int T = N_ / E_;  // threads per pencil
+  __host__ __device__ static constexpr int r(int p) { return p == 0 ? R0_ : p == 1 ? R1_ : p == 2 ? R2_ : R3_; }
+};
+
+// default plans (x- and y-passes)
 template <int N>
 struct FftPlan;
-#define BRAHMS_PLAN(N_, E_, NP_, R0_, R1_, R2_, R3_)                          \
-  template <>                                                                \
-  struct FftPlan<N_> {                                                       \
-    static constexpr int NP = NP_;                                           \
-    static constexpr int E = E_;                                             \
-    static constexpr int r(int p) {                                          \
-      return p == 0 ? R0_ : p == 1 ? R1_ : p == 2 ? R2_ : R3_;               \
-    }                                                                        \
-  };
-BRAHMS_PLAN(2, 2, 1, 2, 0, 0, 0)
-BRAHMS_PLAN(4, 4, 1, 4, 0, 0, 0)
-BRAHMS_PLAN(8, 8, 1, 8, 0, 0, 0)
-BRAHMS_PLAN(16, 16, 1, 16, 0, 0, 0)
-BRAHMS_PLAN(32, 8, 2, 4, 8, 0, 0)
-BRAHMS_PLAN(64, 8, 2, 8, 8, 0, 0)
-BRAHMS_PLAN(128, 16, 2, 16, 8, 0, 0)
-BRAHMS_PLAN(256, 16, 2, 16, 16, 0, 0)
-BRAHMS_PLAN(512, 16, 3, 8, 8, 8, 0)
-BRAHMS_PLAN(1024, 16, 3, 16, 8, 8, 0)
-BRAHMS_PLAN(2048, 16, 3, 16, 16, 8, 0)
-BRAHMS_PLAN(4096, 16, 3, 16, 16, 16, 0)
-BRAHMS_PLAN(6, 6, 2, 3, 2, 0, 0)
-BRAHMS_PLAN(12, 12, 2, 3, 4, 0, 0)
-BRAHMS_PLAN(24, 24, 2, 3, 8, 0, 0)
-BRAHMS_PLAN(48, 12, 3, 3, 4, 4, 0)
-BRAHMS_PLAN(96, 24, 3, 3, 4, 8, 0)
-BRAHMS_PLAN(192, 24, 3, 3, 8, 8, 0)
-BRAHMS_PLAN(384, 24, 4, 3, 8, 4, 4)
-BRAHMS_PLAN(768, 48, 3, 3, 16, 16, 0)
-#undef BRAHMS_PLAN
+template <> struct FftPlan<2> : Plan<2, 2, 1, 2> {};
+template <> struct FftPlan<4> : Plan<4, 4, 1, 4> {};
+template <> struct FftPlan<8> : Plan<8, 8, 1, 8> {};
+template <> struct FftPlan<16> : Plan<16, 16, 1, 16> {};
+template <> struct FftPlan<32> : Plan<32, 8, 2, 4, 8> {};
+template <> struct FftPlan<64> : Plan<64, 8, 2, 8, 8> {};
+template <> struct FftPlan<128> : Plan<128, 16, 2, 16, 8> {};
+template <> struct FftPlan<256> : Plan<256, 16, 2, 16, 16> {};
+template <> struct FftPlan<512> : Plan<512, 16, 3, 8, 8, 8> {};
+template <> struct FftPlan<1024> : Plan<1024, 16, 3, 16, 8, 8> {};
+template <> struct FftPlan<2048> : Plan<2048, 16, 3, 16, 16, 8> {};
+template <> struct FftPlan<4096> : Plan<4096, 16, 3, 16, 16, 16> {};
+template <> struct FftPlan<6> : Plan<6, 6, 2, 3, 2> {};
+template <> struct FftPlan<12> : Plan<12, 12, 2, 3, 4> {};
+template <> struct FftPlan<24> : Plan<24, 24, 2, 3, 8> {};
+template <> struct FftPlan<48> : Plan<48, 12, 3, 3, 4, 4> {};
+template <> struct FftPlan<96> : Plan<96, 24, 3, 3, 4, 8> {};
+template <> struct FftPlan<192> : Plan<192, 24, 3, 3, 8, 8> {};
+template <> struct FftPlan<384> : Plan<384, 24, 4, 3, 8, 4, 4> {};
+template <> struct FftPlan<768> : Plan<768, 48, 3, 3, 16, 16> {};
 
-template <int N, bool INV>
+// tau-pass plans (a 512-point plan with 8 values per thread and 1024-thread
+// tiles measured slower on GB300 than the default, 742 vs 709 us per OPG launch)
+template <int N>
+struct TauPlan : FftPlan<N> {};
+
+template <class PL, bool INV>
 __host__ __device__ constexpr int fft_radix(int p) {
-  return INV ? FftPlan<N>::r(FftPlan<N>::NP - 1 - p) : FftPlan<N>::r(p);
+  return INV ? PL::r(PL::NP - 1 - p) : PL::r(p);
 }
-template <int N, bool INV>
+template <class PL, bool INV>
 __host__ __device__ constexpr int fft_ns(int p) {
   int s = 1;
-  for (int q = 0; q < p; ++q) s *= fft_radix<N, INV>(q);
+  for (int q = 0; q < p; ++q) s *= fft_radix<PL, INV>(q);
   return s;
 }
-// position of input r of butterfly j in the first pass
-template <int N, bool INV>
-__host__ __device__ constexpr int fft_in_stride() { return N / fft_radix<N, INV>(0); }
-// position of output r of butterfly j after the last pass
-template <int N, bool INV>
-__host__ __device__ constexpr int fft_out_stride() { return N / fft_radix<N, INV>(FftPlan<N>::NP - 1); }
 
 // ---------------------------------------------------------------- exchange
 // Contiguous pencil (one row of x): one padding slot per 16 entries.
@@ -250,22 +249,31 @@ struct XchCol {
   __device__ __forceinline__ float2 ld(int pos) const { return base[pos * TX + tx]; }
 };
 
-// Passes P..NP-1 of a length-N transform on the registers v (see header).
-// Every thread of the CTA must call this (it contains __syncthreads()).
 // Twiddle tables hold W_N^k = (c, s) as hi + lo float pairs, float4 (ch, sh,
 // cl, sl): a product with the table is then correctly rounded, so the FFT
 // carries no systematic modulus error from rounded twiddles.
 __device__ __forceinline__ float2 tw_mul(float2 a, float4 w) { return twx<true>(a, w.x, w.z, w.y, w.w); }
 __device__ __forceinline__ float2 tw_mulc(float2 a, float4 w) { return twx<false>(a, w.x, w.z, w.y, w.w); }
 
-template <int N, bool INV, int P, class X>
-__device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const X& x,
-                                        const float4* __restrict__ tw) {
-  constexpr int NP = FftPlan<N>::NP;
-  constexpr int E = FftPlan<N>::E;
-  constexpr int T = N / E;
-  constexpr int R = fft_radix<N, INV>(P);
-  constexpr int NS = fft_ns<N, INV>(P);
+// Barrier used around shared-memory exchanges: the whole CTA, or only the
+// warp when every pencil's threads lie inside one warp.
+struct SyncBlock {
+  __device__ __forceinline__ static void sync() { __syncthreads(); }
+};
+struct SyncWarp {
+  __device__ __forceinline__ static void sync() { __syncwarp(); }
+};
+
+// Passes P..NP-1 of a length-N transform on the registers v (see header).
+// Every thread that shares a barrier of type S must call this.
+template <class PL, bool INV, int P, class X, class S = SyncBlock>
+__device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, const float4* __restrict__ tw) {
+  constexpr int N = PL::N;
+  constexpr int NP = PL::NP;
+  constexpr int E = PL::E;
+  constexpr int T = PL::T;
+  constexpr int R = fft_radix<PL, INV>(P);
+  constexpr int NS = fft_ns<PL, INV>(P);
   constexpr int B = E / R;
   static_assert(E % R == 0, "E must be a multiple of every radix");
   if constexpr (NS > 1) {
@@ -283,9 +291,9 @@ __device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const
 #pragma unroll
   for (int b = 0; b < B; ++b) dft<R, INV>(&v[b * R]);
   if constexpr (P + 1 < NP) {
-    constexpr int R2 = fft_radix<N, INV>(P + 1);
+    constexpr int R2 = fft_radix<PL, INV>(P + 1);
     constexpr int B2 = E / R2;
-    __syncthreads();  // earlier readers of the exchange buffer are done
+    S::sync();  // earlier readers of the exchange buffer are done
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = t + b * T;
@@ -294,14 +302,14 @@ __device__ __forceinline__ void fft_run(float2 (&v)[FftPlan<N>::E], int t, const
 #pragma unroll
       for (int r = 0; r < R; ++r) x.st(d + r * NS, v[b * R + r]);
     }
-    __syncthreads();
+    S::sync();
 #pragma unroll
     for (int b = 0; b < B2; ++b) {
       const int j = t + b * T;
 #pragma unroll
       for (int r = 0; r < R2; ++r) v[b * R2 + r] = x.ld(j + r * (N / R2));
     }
-    fft_run<N, INV, P + 1>(v, t, x, tw);
+    fft_run<PL, INV, P + 1, X, S>(v, t, x, tw);
   }
 }
 

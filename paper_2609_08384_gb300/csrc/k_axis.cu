@@ -13,29 +13,31 @@ static cudaError_t set_smem(K kernel, size_t smem, bool& configured) {
 
 template <int N, bool INV, int AXIS>
 static cudaError_t launch_axis(const AxisArgs& a, cudaStream_t s) {
-  constexpr int TPC = tiles_per_cta<N>();
-  constexpr int THREADS = TPC * fft_threads<N>() * col_tile<N>();
-  const size_t smem = (size_t)axis_smem_floats2<N>() * sizeof(float2);
+  using PL = FftPlan<N>;
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int THREADS = TPC * tile_threads<PL>();
+  const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
   static bool configured = false;
-  cudaError_t e = set_smem(axis_fft_kernel<N, INV, AXIS>, smem, configured);
+  cudaError_t e = set_smem(axis_fft_kernel<PL, INV, AXIS>, smem, configured);
   if (e != cudaSuccess) return e;
   const long long grid = (a.ntiles + TPC - 1) / TPC;
   if (grid <= 0) return cudaSuccess;
-  axis_fft_kernel<N, INV, AXIS><<<(unsigned)grid, THREADS, smem, s>>>(a);
+  axis_fft_kernel<PL, INV, AXIS><<<(unsigned)grid, THREADS, smem, s>>>(a);
   return cudaPeekAtLastError();
 }
 
 template <int N>
 static cudaError_t launch_tprop(const AxisArgs& a, cudaStream_t s) {
-  constexpr int TPC = tiles_per_cta<N>();
-  constexpr int THREADS = TPC * fft_threads<N>() * col_tile<N>();
-  const size_t smem = (size_t)axis_smem_floats2<N>() * sizeof(float2);
+  using PL = TauPlan<N>;
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int THREADS = TPC * tile_threads<PL>();
+  const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
   static bool configured = false;
-  cudaError_t e = set_smem(tpass_prop_kernel<N>, smem, configured);
+  cudaError_t e = set_smem(tpass_prop_kernel<PL>, smem, configured);
   if (e != cudaSuccess) return e;
   const long long grid = (a.ntiles + TPC - 1) / TPC;
   if (grid <= 0) return cudaSuccess;
-  tpass_prop_kernel<N><<<(unsigned)grid, THREADS, smem, s>>>(a);
+  tpass_prop_kernel<PL><<<(unsigned)grid, THREADS, smem, s>>>(a);
   return cudaPeekAtLastError();
 }
 
@@ -68,7 +70,7 @@ int col_tile_of(int n) {
   switch (n) {
 #define BRAHMS_C_CASE(N) \
   case N:                \
-    return col_tile<N>();
+    return col_tile_n(N);
     BRAHMS_FOR_EACH_SIZE(BRAHMS_C_CASE)
 #undef BRAHMS_C_CASE
     default:

@@ -6,7 +6,7 @@ namespace brahms {
 template <int NX, int F>
 static cudaError_t launch_x(const XPassArgs& a, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
-  constexpr int THREADS = ROWS * fft_threads<NX>();
+  constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
   static bool configured = false;
   if (!configured) {

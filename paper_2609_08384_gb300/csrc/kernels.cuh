@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 
 namespace brahms {
@@ -50,27 +52,33 @@ struct AxisArgs {
 
 // ------------------------------------------------------------ tile shapes
 template <int N>
-__host__ __device__ constexpr int fft_threads() { return N / FftPlan<N>::E; }
+__host__ __device__ constexpr int fft_threads() { return FftPlan<N>::T; }
 
+// x-pass CTA: 128 threads (or one row when a row needs more); rows whose
+// threads lie inside one warp synchronise their exchanges with __syncwarp.
 template <int N>
-__host__ __device__ constexpr int xpass_rows() {
-  return fft_threads<N>() >= 256 ? 1 : 256 / fft_threads<N>();
-}
+__host__ __device__ constexpr int xpass_threads() { return fft_threads<N>() >= 128 ? fft_threads<N>() : 128; }
+template <int N>
+__host__ __device__ constexpr int xpass_rows() { return xpass_threads<N>() / fft_threads<N>(); }
+template <int N>
+__host__ __device__ constexpr bool xpass_warp_sync() { return fft_threads<N>() <= 32 && 32 % fft_threads<N>() == 0; }
+// shared memory in float2 units: twiddles (N float4), NL coefficients (6 F),
+// exchange rows, and a private stash of F-1 fields per thread
 template <int N>
 __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
-  return 2 * N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N);
+  return 2 * N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N) + (nf - 1) * FftPlan<N>::E * xpass_threads<N>();
 }
 
-// columns per tile for strided pencils: 128-byte rows up to N = 1024
-template <int N>
-__host__ __device__ constexpr int col_tile() { return N <= 1024 ? 16 : (N <= 2048 ? 8 : 4); }
-template <int N>
-__host__ __device__ constexpr int tiles_per_cta() {
-  return fft_threads<N>() * col_tile<N>() >= 256 ? 1 : 256 / (fft_threads<N>() * col_tile<N>());
-}
-template <int N>
+// Strided pencils: tiles of TX neighbouring columns (128-byte rows up to
+// N = 1024) times the plan's T threads per pencil.
+__host__ __device__ constexpr int col_tile_n(int n) { return n <= 1024 ? 16 : (n <= 2048 ? 8 : 4); }
+template <class PL>
+__host__ __device__ constexpr int tile_threads() { return PL::T * col_tile_n(PL::N); }
+template <class PL>
+__host__ __device__ constexpr int tiles_per_cta() { return tile_threads<PL>() >= 256 ? 1 : 256 / tile_threads<PL>(); }
+template <class PL>
 __host__ __device__ constexpr int axis_smem_floats2() {
-  return 2 * N + tiles_per_cta<N>() * N * col_tile<N>();
+  return 2 * PL::N + tiles_per_cta<PL>() * PL::N * col_tile_n(PL::N);
 }
 
 // -------------------------------------------------------- nonlinear step
@@ -151,20 +159,28 @@ __device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef
 }
 
 // ------------------------------------------------------------------ x-pass
+// One row (y, tau) of every field per T threads.  Fields 0..F-2 are parked in
+// a per-thread shared-memory stash after their inverse transform, so only one
+// field's E values occupy registers at a time; the pointwise RK4 pair reads
+// all F values of a point from the stash and the registers.
 template <int NX, int F>
-__global__ void __launch_bounds__(xpass_rows<NX>() * fft_threads<NX>())
+__global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
     xpass_kernel(const XPassArgs p) {
   constexpr int E = FftPlan<NX>::E;
   constexpr int T = fft_threads<NX>();
+  constexpr int THREADS = xpass_threads<NX>();
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int PITCH = XchRow::pitch(NX);
-  constexpr int RF0 = fft_radix<NX, false>(0);               // forward first radix
-  constexpr int RFL = fft_radix<NX, false>(FftPlan<NX>::NP - 1);  // forward last radix
+  using PL = FftPlan<NX>;
+  constexpr int RF0 = fft_radix<PL, false>(0);            // forward first radix
+  constexpr int RFL = fft_radix<PL, false>(PL::NP - 1);  // forward last radix
   constexpr int SF0 = NX / RF0, SFL = NX / RFL;
+  using SY = typename std::conditional<xpass_warp_sync<NX>(), SyncWarp, SyncBlock>::type;
   extern __shared__ float4 sm4[];
   float4* tw = sm4;
   float2* coef = reinterpret_cast<float2*>(tw + NX);
   float2* xch = coef + 6 * F;
+  float2* stash = xch + ROWS * PITCH + threadIdx.x;  // stash[(f E + e) THREADS]
   for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
   nl_coefficients<F>(p, coef);
   __syncthreads();
@@ -177,31 +193,30 @@ __global__ void __launch_bounds__(xpass_rows<NX>() * fft_threads<NX>())
   const int mode = p.mode;
   const bool from_k = (mode == XM_INV || mode == XM_NL_MID || mode == XM_NL_LAST);
 
-  float2 v[F][E];
+  float2 v[E];
   // The inverse transform's first pass reads positions t + b T + r NX/RFL and
   // ends at t + b T + r NX/RF0, which are the forward transform's first-pass
-  // positions: registers flow from one to the other without an exchange.
-  if (from_k) {
+  // positions: values flow from one to the other without an exchange.
 #pragma unroll
-    for (int f = 0; f < F; ++f) {
-      const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+  for (int f = 0; f < F; ++f) {
+    const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+    if (from_k) {
 #pragma unroll
       for (int b = 0; b < E / RFL; ++b)
 #pragma unroll
         for (int r = 0; r < RFL; ++r)
-          v[f][b * RFL + r] = act ? src[t + b * T + r * SFL] : make_float2(0.f, 0.f);
-    }
-#pragma unroll
-    for (int f = 0; f < F; ++f) fft_run<NX, true, 0>(v[f], t, xr, tw);
-  } else {
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-      const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+          v[b * RFL + r] = act ? src[t + b * T + r * SFL] : make_float2(0.f, 0.f);
+      fft_run<PL, true, 0, XchRow, SY>(v, t, xr, tw);
+    } else {
 #pragma unroll
       for (int b = 0; b < E / RF0; ++b)
 #pragma unroll
         for (int r = 0; r < RF0; ++r)
-          v[f][b * RF0 + r] = act ? src[t + b * T + r * SF0] : make_float2(0.f, 0.f);
+          v[b * RF0 + r] = act ? src[t + b * T + r * SF0] : make_float2(0.f, 0.f);
+    }
+    if (f < F - 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) stash[(f * E + e) * THREADS] = v[e];
     }
   }
 
@@ -210,37 +225,40 @@ __global__ void __launch_bounds__(xpass_rows<NX>() * fft_threads<NX>())
     for (int e = 0; e < E; ++e) {
       float2 a[F];
 #pragma unroll
-      for (int f = 0; f < F; ++f) a[f] = v[f][e];
+      for (int f = 0; f < F - 1; ++f) a[f] = stash[(f * E + e) * THREADS];
+      a[F - 1] = v[e];
       if (mode != XM_NL_FIRST) rk4<F>(a, coef);
       if (mode != XM_NL_LAST) rk4<F>(a, coef + 3 * F);
 #pragma unroll
-      for (int f = 0; f < F; ++f) v[f][e] = a[f];
+      for (int f = 0; f < F - 1; ++f) stash[(f * E + e) * THREADS] = a[f];
+      v[e] = a[F - 1];
     }
   }
 
-  if (mode == XM_INV || mode == XM_NL_LAST) {
-    const float sc = mode == XM_INV ? p.scale : 1.f;
-    if (act) {
+  const bool to_x = (mode == XM_INV || mode == XM_NL_LAST);
+  const float sc = mode == XM_INV ? p.scale : 1.f;
 #pragma unroll
-      for (int f = 0; f < F; ++f) {
-        float2* dst = p.data + f * p.fstride + row * NX;
+  for (int g = 0; g < F; ++g) {
+    const int f = (g + F - 1) % F;  // the field in registers first, then the stash
+    if (f < F - 1) {
+#pragma unroll
+      for (int e = 0; e < E; ++e) v[e] = stash[(f * E + e) * THREADS];
+    }
+    float2* dst = p.data + f * p.fstride + (act ? row : 0) * NX;
+    if (to_x) {
+      if (act) {
 #pragma unroll
         for (int b = 0; b < E / RF0; ++b)
 #pragma unroll
-          for (int r = 0; r < RF0; ++r) dst[t + b * T + r * SF0] = cscale(v[f][b * RF0 + r], sc);
+          for (int r = 0; r < RF0; ++r) dst[t + b * T + r * SF0] = cscale(v[b * RF0 + r], sc);
       }
-    }
-  } else {
-#pragma unroll
-    for (int f = 0; f < F; ++f) fft_run<NX, false, 0>(v[f], t, xr, tw);
-    if (act) {
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-        float2* dst = p.data + f * p.fstride + row * NX;
+    } else {
+      fft_run<PL, false, 0, XchRow, SY>(v, t, xr, tw);
+      if (act) {
 #pragma unroll
         for (int b = 0; b < E / RFL; ++b)
 #pragma unroll
-          for (int r = 0; r < RFL; ++r) dst[t + b * T + r * SFL] = v[f][b * RFL + r];
+          for (int r = 0; r < RFL; ++r) dst[t + b * T + r * SFL] = v[b * RFL + r];
       }
     }
   }
@@ -256,7 +274,7 @@ struct AxisTile {
   int f, other, x;
   bool act;
   __device__ __forceinline__ AxisTile(const AxisArgs& p, long long tile, int tx) {
-    constexpr int TX = col_tile<N>();
+    constexpr int TX = col_tile_n(N);
     const int xt = (int)(tile % p.xtiles);
     const long long rest = tile / p.xtiles;
     const int no = AXIS == 1 ? p.nt : p.ny;
@@ -270,12 +288,12 @@ struct AxisTile {
   }
 };
 
-template <int N, bool INV, int AXIS>
-__global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_tile<N>())
+template <class PL, bool INV, int AXIS>
+__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
     axis_fft_kernel(const AxisArgs p) {
-  constexpr int E = FftPlan<N>::E, T = fft_threads<N>(), TX = col_tile<N>();
-  constexpr int TPC = tiles_per_cta<N>();
-  constexpr int R0 = fft_radix<N, INV>(0), RL = fft_radix<N, INV>(FftPlan<N>::NP - 1);
+  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int R0 = fft_radix<PL, INV>(0), RL = fft_radix<PL, INV>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
   extern __shared__ float4 sm4[];
   float4* tw = sm4;
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
 #pragma unroll
     for (int r = 0; r < R0; ++r)
       v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
-  fft_run<N, INV, 0>(v, t, xc, tw);
+  fft_run<PL, INV, 0>(v, t, xc, tw);
   if (a.act) {
 #pragma unroll
     for (int b = 0; b < E / RL; ++b)
@@ -302,12 +320,12 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
 }
 
 // Forward tau-FFT, propagator multiply, inverse tau-FFT, in one pass.
-template <int N>
-__global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_tile<N>())
+template <class PL>
+__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
     tpass_prop_kernel(const AxisArgs p) {
-  constexpr int E = FftPlan<N>::E, T = fft_threads<N>(), TX = col_tile<N>();
-  constexpr int TPC = tiles_per_cta<N>();
-  constexpr int R0 = fft_radix<N, false>(0), RL = fft_radix<N, false>(FftPlan<N>::NP - 1);
+  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int R0 = fft_radix<PL, false>(0), RL = fft_radix<PL, false>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
   extern __shared__ float4 sm4[];
   float4* tw = sm4;
@@ -324,7 +342,7 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
 #pragma unroll
     for (int r = 0; r < R0; ++r)
       v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
-  fft_run<N, false, 0>(v, t, xc, tw);
+  fft_run<PL, false, 0>(v, t, xc, tw);
   // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL.
   // P = (1 + Dx)(1 + Dy)(1 + Dt) applied as w + w D with w = v/(nx ny nt).
   float2 dxy = make_float2(0.f, 0.f);
@@ -345,7 +363,7 @@ __global__ void __launch_bounds__(tiles_per_cta<N>() * fft_threads<N>() * col_ti
       v[b * RL + r] = cadd(w, cmul(w, d));
     }
   // the inverse's first pass reads exactly these positions
-  fft_run<N, true, 0>(v, t, xc, tw);
+  fft_run<PL, true, 0>(v, t, xc, tw);
   if (a.act) {
 #pragma unroll
     for (int b = 0; b < E / R0; ++b)
