@@ -126,6 +126,68 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
 /* Number of kernel launches this context has enqueued since creation. */
 long long brahms_launch_count(const brahms_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched form (two-field SHG sweeps): many independent simulations of
+ * uneven grids, mismatch and crystal length advanced by one persistent
+ * cooperative kernel whose launch is captured in a CUDA graph.  Each instance
+ * follows the same split step as brahms_propagate (constant dk per instance,
+ * starting at z = 0 with Phi = 0).  Shapes (nx = ny, nt) must be one of
+ * (32,64), (64,128), (96,192), (128,256) (else E_SIZE).  The batch allocates
+ * its own device memory (state and tables per instance).  Work is enqueued on
+ * cuda_stream (NULL = legacy default stream).
+ * ---------------------------------------------------------------------- */
+typedef struct brahms_batch brahms_batch;
+
+/* Create an empty batch. */
+brahms_status brahms_batch_create(brahms_batch** out, void* cuda_stream);
+
+/* Add one SHG instance (fields SH, F; fp holds 2 records) that will run nz
+ * steps of dz [m]; *index receives its position.  Tables are built here. */
+brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double dx, double dy, double dt,
+                               const brahms_field_params* fp, double d_eff, double dk, int nz, double dz,
+                               int* index);
+
+/* Copy instance `index`'s initial envelopes in: 2 pointers to nt*ny*nx
+ * complex64 values, device (on_device != 0) or host memory (copied before
+ * return).  Every instance needs fields before brahms_batch_run. */
+brahms_status brahms_batch_set_fields(brahms_batch* b, int index, const void* const* fields, int dtype,
+                                      int on_device);
+
+/* Tile schedule of one shape (0..3 in the order above): CTA tiles per work
+ * item for the x-, y- and tau-passes (1..64). */
+brahms_status brahms_batch_set_granularity(brahms_batch* b, int shape, int gx, int gy, int gt);
+
+/* Autotune the schedule: per shape the tiles per item (1, 2, 4), then CTAs
+ * per SM (1, 2), each timed on the whole batch with every instance capped at
+ * tune_steps steps; instance fields are restored afterwards.  Waits for the
+ * stream.  *best_ms (nullable) receives the best capped run time. */
+brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms);
+
+/* The current schedule of one shape. */
+brahms_status brahms_batch_get_schedule(const brahms_batch* b, int shape, int* gx, int* gy, int* gt,
+                                        int* ctas_per_sm);
+
+/* Advance every instance through all of its nz steps (z = 0 to nz dz) in one
+ * graph launch: counter reset + the persistent kernel.  Asynchronous. */
+brahms_status brahms_batch_run(brahms_batch* b);
+
+/* Wait for the stream; E_TIMEOUT if the persistent kernel gave up waiting
+ * for a pass of some instance (its bounded waits expired). */
+brahms_status brahms_batch_sync(brahms_batch* b);
+
+/* Copy instance `index`'s envelopes out (2 pointers, complex64); waits. */
+brahms_status brahms_batch_get_fields(brahms_batch* b, int index, void* const* out, int dtype, int on_device);
+
+/* Instances, persistent grid size, threads per CTA, graph launches so far. */
+brahms_status brahms_batch_info(const brahms_batch* b, int* ninstances, int* grid, int* threads,
+                                long long* launches);
+
+/* Release the batch and its device memory. */
+void brahms_batch_free(brahms_batch* b);
+
+/* Last error message of the batch. */
+const char* brahms_batch_last_error(const brahms_batch* b);
+
 /* Allocation-free energy of caller-owned device fields.  (The paper has no
  * counterpart; this serves callers that cannot let the library allocate
  * device memory: hosts whose GPU memory is all owned by another allocator,

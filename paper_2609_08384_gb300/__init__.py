@@ -60,6 +60,22 @@ SIGNATURES = {
     "brahms_launch_count": (_c.c_longlong, [_vp]),
     "brahms_energy_static": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double,
                                         _c.c_double, _c.c_double, _c.POINTER(FieldParams), _vp, _vp]),
+    "brahms_batch_create": (_c.c_int, [_c.POINTER(_vp), _vp]),
+    "brahms_batch_add": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double,
+                                    _c.POINTER(FieldParams), _c.c_double, _c.c_double, _c.c_int, _c.c_double,
+                                    _c.POINTER(_c.c_int)]),
+    "brahms_batch_set_fields": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_vp), _c.c_int, _c.c_int]),
+    "brahms_batch_set_granularity": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
+    "brahms_batch_tune": (_c.c_int, [_vp, _c.c_int, _dp]),
+    "brahms_batch_get_schedule": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
+                                             _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "brahms_batch_run": (_c.c_int, [_vp]),
+    "brahms_batch_sync": (_c.c_int, [_vp]),
+    "brahms_batch_get_fields": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_vp), _c.c_int, _c.c_int]),
+    "brahms_batch_info": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
+                                     _llp]),
+    "brahms_batch_free": (None, [_vp]),
+    "brahms_batch_last_error": (_c.c_char_p, [_vp]),
     "brahms_free": (None, [_vp]),
     "brahms_last_error": (_c.c_char_p, [_vp]),
     "brahms_status_string": (_c.c_char_p, [_c.c_int]),
@@ -256,3 +272,97 @@ class Solver:
         else:
             raise ValueError("fields must be complex64 or complex128")
         return ptrs, dt, dev
+
+
+class Batch:
+    """A batch of two-field SHG instances advanced by one persistent launch
+    (brahms_batch_* entry points)."""
+
+    def __init__(self, stream=None):
+        import torch
+
+        lib = load()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = _vp()
+        _check(None, lib.brahms_batch_create(ctypes.byref(h), _vp(self.stream.cuda_stream)))
+        self.h = h
+        self.shapes = []
+
+    def _chk(self, s):
+        if s != BRAHMS_OK:
+            raise BrahmsError(s, load().brahms_batch_last_error(self.h).decode())
+
+    def add(self, grid, fields, d_eff, dk, nz, dz) -> int:
+        fp = (FieldParams * 2)(*[field_params(f) for f in fields])
+        idx = ctypes.c_int()
+        self._chk(load().brahms_batch_add(self.h, grid.nx, grid.ny, grid.nt, grid.dx, grid.dy, grid.dt, fp,
+                                          float(d_eff), float(dk), int(nz), float(dz), ctypes.byref(idx)))
+        self.shapes.append((grid.nt, grid.ny, grid.nx))
+        return idx.value
+
+    def set_fields(self, index, fields):
+        """fields: two contiguous complex64 torch tensors (cuda) or numpy arrays."""
+        import torch
+
+        ptrs, dev = [], None
+        for a in fields:
+            if isinstance(a, torch.Tensor):
+                assert a.dtype == torch.complex64 and a.is_contiguous()
+                ptrs.append(a.data_ptr())
+                dev = a.is_cuda
+            else:
+                a = np.ascontiguousarray(a, dtype=np.complex64)
+                ptrs.append(a.ctypes.data)
+                dev = False
+        self._chk(load().brahms_batch_set_fields(self.h, int(index), _ptr_array(ptrs), BRAHMS_C64, int(bool(dev))))
+
+    def set_granularity(self, shape, gx, gy, gt):
+        self._chk(load().brahms_batch_set_granularity(self.h, shape, gx, gy, gt))
+
+    def tune(self, tune_steps=16) -> float:
+        ms = ctypes.c_double()
+        self._chk(load().brahms_batch_tune(self.h, int(tune_steps), ctypes.byref(ms)))
+        return ms.value
+
+    def schedule(self, shape):
+        v = [ctypes.c_int() for _ in range(4)]
+        self._chk(load().brahms_batch_get_schedule(self.h, shape, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def run(self):
+        self._chk(load().brahms_batch_run(self.h))
+
+    def sync(self):
+        self._chk(load().brahms_batch_sync(self.h))
+
+    def get_fields(self, index, on_device=False):
+        import torch
+
+        shape = self.shapes[index]
+        if on_device:
+            out = [torch.empty(shape, dtype=torch.complex64, device="cuda") for _ in range(2)]
+            ptrs = [t.data_ptr() for t in out]
+        else:
+            out = [np.empty(shape, dtype=np.complex64) for _ in range(2)]
+            ptrs = [a.ctypes.data for a in out]
+        self._chk(load().brahms_batch_get_fields(self.h, int(index), _ptr_array(ptrs), BRAHMS_C64,
+                                                 int(bool(on_device))))
+        return out
+
+    def info(self):
+        n, g, t = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        l = ctypes.c_longlong()
+        self._chk(load().brahms_batch_info(self.h, ctypes.byref(n), ctypes.byref(g), ctypes.byref(t),
+                                           ctypes.byref(l)))
+        return {"instances": n.value, "grid": g.value, "threads": t.value, "launches": l.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().brahms_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

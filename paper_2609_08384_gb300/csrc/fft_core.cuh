@@ -209,12 +209,12 @@ template <> struct FftPlan<2048> : Plan<2048, 16, 3, 16, 16, 8> {};
 template <> struct FftPlan<4096> : Plan<4096, 16, 3, 16, 16, 16> {};
 template <> struct FftPlan<6> : Plan<6, 6, 2, 3, 2> {};
 template <> struct FftPlan<12> : Plan<12, 12, 2, 3, 4> {};
-template <> struct FftPlan<24> : Plan<24, 24, 2, 3, 8> {};
+template <> struct FftPlan<24> : Plan<24, 12, 3, 3, 2, 4> {};
 template <> struct FftPlan<48> : Plan<48, 12, 3, 3, 4, 4> {};
-template <> struct FftPlan<96> : Plan<96, 24, 3, 3, 4, 8> {};
-template <> struct FftPlan<192> : Plan<192, 24, 3, 3, 8, 8> {};
+template <> struct FftPlan<96> : Plan<96, 12, 4, 3, 4, 4, 2> {};
+template <> struct FftPlan<192> : Plan<192, 12, 4, 3, 4, 4, 4> {};
 template <> struct FftPlan<384> : Plan<384, 24, 4, 3, 8, 4, 4> {};
-template <> struct FftPlan<768> : Plan<768, 48, 3, 3, 16, 16> {};
+template <> struct FftPlan<768> : Plan<768, 24, 4, 3, 4, 8, 8> {};
 
 // tau-pass plans (a 512-point plan with 8 values per thread and 1024-thread
 // tiles measured slower on GB300 than the default, 742 vs 709 us per OPG launch)

@@ -67,7 +67,7 @@ __host__ __device__ constexpr bool xpass_warp_sync() { return fft_threads<N>() <
 template <int N>
 __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
   return 2 * N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N) + (nf - 1) * FftPlan<N>::E * xpass_threads<N>();
-}
+}  // equals xtile_smem_floats2<N, xpass_threads<N>()>(nf)
 
 // Strided pencils: tiles of TX neighbouring columns (128-byte rows up to
 // N = 1024) times the plan's T threads per pencil.
@@ -159,35 +159,37 @@ __device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef
 }
 
 // ------------------------------------------------------------------ x-pass
-// One row (y, tau) of every field per T threads.  Fields 0..F-2 are parked in
-// a per-thread shared-memory stash after their inverse transform, so only one
-// field's E values occupy registers at a time; the pointwise RK4 pair reads
-// all F values of a point from the stash and the registers.
-template <int NX, int F>
-__global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
-    xpass_kernel(const XPassArgs p) {
-  constexpr int E = FftPlan<NX>::E;
-  constexpr int T = fft_threads<NX>();
-  constexpr int THREADS = xpass_threads<NX>();
-  constexpr int ROWS = xpass_rows<NX>();
-  constexpr int PITCH = XchRow::pitch(NX);
+// One row (y, tau) of every field per T threads; a CTA of THREADS threads
+// handles THREADS/T rows per tile.  Fields 0..F-2 are parked in a per-thread
+// shared-memory stash after their inverse transform, so only one field's E
+// values occupy registers at a time; the pointwise RK4 pair reads all F
+// values of a point from the stash and the registers.  Field data is read
+// with ld.global.cg (L2), so a tile may follow a pass written by other SMs.
+template <int NX, int THREADS>
+__host__ __device__ constexpr int xtile_rows() { return THREADS / FftPlan<NX>::T; }
+template <int NX, int THREADS>
+__host__ __device__ constexpr int xtile_smem_floats2(int nf) {
+  return 2 * NX + 6 * nf + xtile_rows<NX, THREADS>() * XchRow::pitch(NX) + (nf - 1) * FftPlan<NX>::E * THREADS;
+}
+
+template <int NX, int F, int THREADS>
+__device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, const float4* tw,
+                                           const float2* coef, float2* xch, float2* stash_all) {
   using PL = FftPlan<NX>;
-  constexpr int RF0 = fft_radix<PL, false>(0);            // forward first radix
+  constexpr int E = PL::E;
+  constexpr int T = PL::T;
+  constexpr int ROWS = xtile_rows<NX, THREADS>();
+  constexpr int PITCH = XchRow::pitch(NX);
+  constexpr int RF0 = fft_radix<PL, false>(0);           // forward first radix
   constexpr int RFL = fft_radix<PL, false>(PL::NP - 1);  // forward last radix
   constexpr int SF0 = NX / RF0, SFL = NX / RFL;
   using SY = typename std::conditional<xpass_warp_sync<NX>(), SyncWarp, SyncBlock>::type;
-  extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* coef = reinterpret_cast<float2*>(tw + NX);
-  float2* xch = coef + 6 * F;
-  float2* stash = xch + ROWS * PITCH + threadIdx.x;  // stash[(f E + e) THREADS]
-  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
-  nl_coefficients<F>(p, coef);
-  __syncthreads();
+  static_assert(ROWS >= 1 && ROWS * T == THREADS, "CTA must hold whole rows");
+  float2* stash = stash_all + threadIdx.x;  // stash[(f E + e) THREADS]
 
   const int t = threadIdx.x % T;
   const int rl = threadIdx.x / T;
-  const long long row = (long long)blockIdx.x * ROWS + rl;
+  const long long row = tile * ROWS + rl;
   const bool act = row < p.rows;
   const XchRow xr{xch + rl * PITCH};
   const int mode = p.mode;
@@ -205,14 +207,14 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
       for (int b = 0; b < E / RFL; ++b)
 #pragma unroll
         for (int r = 0; r < RFL; ++r)
-          v[b * RFL + r] = act ? src[t + b * T + r * SFL] : make_float2(0.f, 0.f);
+          v[b * RFL + r] = act ? __ldcg(src + t + b * T + r * SFL) : make_float2(0.f, 0.f);
       fft_run<PL, true, 0, XchRow, SY>(v, t, xr, tw);
     } else {
 #pragma unroll
       for (int b = 0; b < E / RF0; ++b)
 #pragma unroll
         for (int r = 0; r < RF0; ++r)
-          v[b * RF0 + r] = act ? src[t + b * T + r * SF0] : make_float2(0.f, 0.f);
+          v[b * RF0 + r] = act ? __ldcg(src + t + b * T + r * SF0) : make_float2(0.f, 0.f);
     }
     if (f < F - 1) {
 #pragma unroll
@@ -264,6 +266,21 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
   }
 }
 
+template <int NX, int F>
+__global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
+    xpass_kernel(const XPassArgs p) {
+  constexpr int THREADS = xpass_threads<NX>();
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* coef = reinterpret_cast<float2*>(tw + NX);
+  float2* xch = coef + 6 * F;
+  float2* stash = xch + xtile_rows<NX, THREADS>() * XchRow::pitch(NX);
+  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
+  nl_coefficients<F>(p, coef);
+  __syncthreads();
+  xpass_tile<NX, F, THREADS>(p, blockIdx.x, tw, coef, xch, stash);
+}
+
 // ------------------------------------------------- strided-axis passes
 // AXIS 1: pencils along y (stride nx), tiles over (f, tau, x-tile).
 // AXIS 2: pencils along tau (stride nx ny), tiles over (f, y, x-tile).
@@ -288,28 +305,27 @@ struct AxisTile {
   }
 };
 
-template <class PL, bool INV, int AXIS>
-__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
-    axis_fft_kernel(const AxisArgs p) {
+// Tiles per CTA of THREADS threads for strided pencils.
+template <class PL, int THREADS>
+__host__ __device__ constexpr int tiles_per_cta_t() { return THREADS / tile_threads<PL>(); }
+
+template <class PL, bool INV, int AXIS, int THREADS>
+__device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile, const float4* tw, float2* xch) {
   constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
-  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
+  static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
   constexpr int R0 = fft_radix<PL, INV>(0), RL = fft_radix<PL, INV>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
-  extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* xch = reinterpret_cast<float2*>(tw + N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
-  __syncthreads();
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
   const int tx = lt % TX, t = lt / TX;
-  const AxisTile<N, AXIS> a(p, (long long)blockIdx.x * TPC + tl, tx);
+  const AxisTile<N, AXIS> a(p, cta_tile * TPC + tl, tx);
   const XchCol<TX> xc{xch + tl * N * TX, tx};
   float2 v[E];
 #pragma unroll
   for (int b = 0; b < E / R0; ++b)
 #pragma unroll
     for (int r = 0; r < R0; ++r)
-      v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
+      v[b * R0 + r] = a.act ? __ldcg(a.base + (t + b * T + r * S0) * a.stride) : make_float2(0.f, 0.f);
   fft_run<PL, INV, 0>(v, t, xc, tw);
   if (a.act) {
 #pragma unroll
@@ -320,28 +336,23 @@ __global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
 }
 
 // Forward tau-FFT, propagator multiply, inverse tau-FFT, in one pass.
-template <class PL>
-__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
-    tpass_prop_kernel(const AxisArgs p) {
+template <class PL, int THREADS>
+__device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile, const float4* tw, float2* xch) {
   constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
-  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
+  static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
   constexpr int R0 = fft_radix<PL, false>(0), RL = fft_radix<PL, false>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
-  extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* xch = reinterpret_cast<float2*>(tw + N);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = p.tw[i];
-  __syncthreads();
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
   const int tx = lt % TX, t = lt / TX;
-  const AxisTile<N, 2> a(p, (long long)blockIdx.x * TPC + tl, tx);
+  const AxisTile<N, 2> a(p, cta_tile * TPC + tl, tx);
   const XchCol<TX> xc{xch + tl * N * TX, tx};
   float2 v[E];
 #pragma unroll
   for (int b = 0; b < E / R0; ++b)
 #pragma unroll
     for (int r = 0; r < R0; ++r)
-      v[b * R0 + r] = a.act ? a.base[(t + b * T + r * S0) * a.stride] : make_float2(0.f, 0.f);
+      v[b * R0 + r] = a.act ? __ldcg(a.base + (t + b * T + r * S0) * a.stride) : make_float2(0.f, 0.f);
   fft_run<PL, false, 0>(v, t, xc, tw);
   // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL.
   // P = (1 + Dx)(1 + Dy)(1 + Dt) applied as w + w D with w = v/(nx ny nt).
@@ -370,6 +381,30 @@ __global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
 #pragma unroll
       for (int r = 0; r < R0; ++r) a.base[(t + b * T + r * S0) * a.stride] = v[b * R0 + r];
   }
+}
+
+template <class PL, bool INV, int AXIS>
+__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
+    axis_fft_kernel(const AxisArgs p) {
+  constexpr int THREADS = tiles_per_cta<PL>() * tile_threads<PL>();
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* xch = reinterpret_cast<float2*>(tw + PL::N);
+  for (int i = threadIdx.x; i < PL::N; i += blockDim.x) tw[i] = p.tw[i];
+  __syncthreads();
+  axis_tile<PL, INV, AXIS, THREADS>(p, blockIdx.x, tw, xch);
+}
+
+template <class PL>
+__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
+    tpass_prop_kernel(const AxisArgs p) {
+  constexpr int THREADS = tiles_per_cta<PL>() * tile_threads<PL>();
+  extern __shared__ float4 sm4[];
+  float4* tw = sm4;
+  float2* xch = reinterpret_cast<float2*>(tw + PL::N);
+  for (int i = threadIdx.x; i < PL::N; i += blockDim.x) tw[i] = p.tw[i];
+  __syncthreads();
+  tprop_tile<PL, THREADS>(p, blockIdx.x, tw, xch);
 }
 
 // ------------------------------------------------------------ dispatchers
