@@ -17,6 +17,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   propagate           energy and Manley-Rowe invariants, second-order
                       self-convergence in dz
   energy              analytic Gaussian-beam/pulse energy
+  adjoint_gradient    dot-product identities (linear step; RK4 against an
+                      independent tangent-linear RK4), stage-phase
+                      sensitivities and full gradients against central
+                      finite differences of objective()
 """
 from __future__ import annotations
 
@@ -85,6 +89,19 @@ def _load():
             lib.orc_propagate.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp]
             lib.orc_propagate.restype = ctypes.c_int
             lib.orc_energy.argtypes = [P(_Problem), vp, dp, dp]
+            lib.orc_rk4_jvp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              vp, vp, vp, vp]
+            lib.orc_rk4_vjp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                              vp, vp, vp, dp]
+            lib.orc_linear_step_adjoint.argtypes = [P(_Problem), vp, ctypes.c_double]
+            lib.orc_spectral_phase.argtypes = [P(_Problem), vp, dp, ctypes.c_int]
+            lib.orc_nonlinear_step_adjoint.argtypes = [P(_Problem), vp, vp, ctypes.c_double, ctypes.c_double,
+                                                       ctypes.c_double, dp]
+            lib.orc_adjoint_gradient.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp,
+                                                 ctypes.c_int, dp, dp, dp]
+            lib.orc_adjoint_gradient.restype = ctypes.c_double
+            lib.orc_objective.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, dp]
+            lib.orc_objective.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -184,3 +201,73 @@ def energy(prob: _Problem, fields: Sequence[np.ndarray]):
 def problem_from(p) -> _Problem:
     """Oracle problem struct from a workloads.Problem."""
     return make_problem(p.grid, p.fields, p.d_eff)
+
+
+# --------------------------------------------------------------- adjoint
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _kap(prob):
+    return np.array([kappa(prob, f) for f in range(prob.nf)] + [0.0] * (3 - prob.nf))
+
+
+def rk4_jvp_point(prob, phi_a, dk, h, x, dx):
+    """Tangent of one RK4 step at one point: returns (y, dy)."""
+    x = _c128(x)
+    dx = _c128(dx)
+    y = np.zeros(3, complex)
+    dy = np.zeros(3, complex)
+    k = _kap(prob)
+    _load().orc_rk4_jvp_point(prob.nf, _dptr(k), phi_a, dk, h, x.ctypes.data, dx.ctypes.data, y.ctypes.data,
+                              dy.ctypes.data)
+    return y[:prob.nf], dy[:prob.nf]
+
+
+def rk4_vjp_point(prob, phi_a, dk, h, x, gy):
+    """Adjoint of one RK4 step at one point: returns (gx, sens[3])."""
+    x = _c128(x)
+    gy = _c128(gy)
+    gx = np.zeros(3, complex)
+    sens = np.zeros(3)
+    k = _kap(prob)
+    _load().orc_rk4_vjp_point(prob.nf, _dptr(k), phi_a, dk, h, x.ctypes.data, gy.ctypes.data, gx.ctypes.data,
+                              _dptr(sens))
+    return gx[:prob.nf], sens
+
+
+def linear_step_adjoint(prob, fields, dz):
+    a = _stack(fields)
+    _load().orc_linear_step_adjoint(ctypes.byref(prob), a.ctypes.data, dz)
+    return a
+
+
+def spectral_phase(prob, field, phi, sign=+1):
+    a = _c128(field).copy()
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    _load().orc_spectral_phase(ctypes.byref(prob), a.ctypes.data, _dptr(ph), int(sign))
+    return a
+
+
+def objective(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1):
+    a = _stack(fields)
+    dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    return float(_load().orc_objective(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
+                                       _dptr(ph), int(phi_field), _dptr(w)))
+
+
+def adjoint_gradient(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1):
+    """J = sum_f w_f sum |A_f(L)|^2 and its gradient with respect to the
+    spectral phase phi (centred order, applied to field phi_field) and the
+    per-step mismatch.  Returns (J, grad_phi or None, grad_dk)."""
+    a = _stack(fields)
+    dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    gphi = None if phi is None else np.zeros(prob.nt)
+    gdk = np.zeros(nz)
+    J = _load().orc_adjoint_gradient(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
+                                     _dptr(ph), int(phi_field), _dptr(w), _dptr(gphi), _dptr(gdk))
+    return float(J), gphi, gdk

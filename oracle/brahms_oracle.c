@@ -411,3 +411,345 @@ void orc_energy(const orc_problem* pb, const cplx* fields, double* energy, doubl
     }
   }
 }
+
+/* ======================================================================== */
+/* Discrete adjoint (reverse mode) of the split-step propagation.            */
+/*                                                                            */
+/* Objective J = sum_f w_f sum_points |A_f(L)|^2 (real).  For complex        */
+/* variables the gradient is G_z = dJ/dRe z + i dJ/dIm z = 2 dJ/d conj(z);    */
+/* for y = f(x):  G_x = sum_y [ conj(G_y) dy/d conj(x) + G_y conj(dy/dx) ].   */
+/* The linear step is complex-linear, so its adjoint is IDFT3(conj(P) DFT3).  */
+/* The RK4 half step is differentiated stage by stage (reverse order).        */
+/* The mismatch enters every RK4 stage through Phi(z) = Phi_j + dk_j (z-z_j); */
+/* dJ/dPhi at a stage is Re sum conj(G_k) dk/dPhi with dk/dPhi = -/+ i k.     */
+/* ======================================================================== */
+
+/* Coupling coefficients c_f = i kap_f e^{-/+ i phi} (minus for field 0). */
+static void nl_coef(int nf, const double* kap, double phi, cplx* c) {
+  cplx em = cexp(-I * phi), ep = cexp(I * phi);
+  if (nf == 3) {
+    c[0] = I * kap[0] * em;
+    c[1] = I * kap[1] * ep;
+    c[2] = I * kap[2] * ep;
+  } else {
+    c[0] = I * (0.5 * kap[0]) * em;
+    c[1] = I * kap[1] * ep;
+  }
+}
+
+/* f(u) with coefficients c (the right-hand sides of nl_rhs). */
+static void rhs_c(int nf, const cplx* c, const cplx* u, cplx* k) {
+  if (nf == 3) {
+    k[0] = c[0] * u[1] * u[2];
+    k[1] = c[1] * u[0] * conj(u[2]);
+    k[2] = c[2] * u[0] * conj(u[1]);
+  } else {
+    k[0] = c[0] * u[1] * u[1];
+    k[1] = c[1] * u[0] * conj(u[1]);
+  }
+}
+
+/* tangent: df = sum df/du du + df/dconj(u) conj(du) */
+static void rhs_jvp(int nf, const cplx* c, const cplx* u, const cplx* du, cplx* dk) {
+  if (nf == 3) {
+    dk[0] = c[0] * (du[1] * u[2] + u[1] * du[2]);
+    dk[1] = c[1] * (du[0] * conj(u[2]) + u[0] * conj(du[2]));
+    dk[2] = c[2] * (du[0] * conj(u[1]) + u[0] * conj(du[1]));
+  } else {
+    dk[0] = c[0] * 2.0 * u[1] * du[1];
+    dk[1] = c[1] * (du[0] * conj(u[1]) + u[0] * conj(du[1]));
+  }
+}
+
+/* adjoint: gu += sum_y [ conj(g_y) dy/dconj(u) + g_y conj(dy/du) ] */
+static void rhs_vjp(int nf, const cplx* c, const cplx* u, const cplx* g, cplx* gu) {
+  if (nf == 3) {
+    gu[0] += g[1] * conj(c[1]) * u[2] + g[2] * conj(c[2]) * u[1];
+    gu[1] += g[0] * conj(c[0]) * conj(u[2]) + conj(g[2]) * c[2] * u[0];
+    gu[2] += g[0] * conj(c[0]) * conj(u[1]) + conj(g[1]) * c[1] * u[0];
+  } else {
+    gu[0] += g[1] * conj(c[1]) * u[1];
+    gu[1] += g[0] * conj(2.0 * c[0] * u[1]) + conj(g[1]) * c[1] * u[0];
+  }
+}
+
+/* sum_f Re( conj(g_f) dk_f/dPhi ),  dk_0/dPhi = -i k_0, others +i k_f */
+static double phase_sens(int nf, const cplx* g, const cplx* k) {
+  double s = creal(conj(g[0]) * (-I * k[0]));
+  for (int f = 1; f < nf; ++f) s += creal(conj(g[f]) * (I * k[f]));
+  return s;
+}
+
+/* Tangent of one RK4 step from z_a over h (same stages as orc_rk4_point). */
+void orc_rk4_jvp_point(int nf, const double* kap, double phi_a, double dk, double h, const cplx* x,
+                       const cplx* dx, cplx* y, cplx* dy) {
+  cplx c1[3], c2[3], c3[3], u[3], du[3], k[4][3], dkk[4][3];
+  nl_coef(nf, kap, phi_a, c1);
+  nl_coef(nf, kap, phi_a + dk * 0.5 * h, c2);
+  nl_coef(nf, kap, phi_a + dk * h, c3);
+  rhs_c(nf, c1, x, k[0]);
+  rhs_jvp(nf, c1, x, dx, dkk[0]);
+  for (int f = 0; f < nf; ++f) { u[f] = x[f] + 0.5 * h * k[0][f]; du[f] = dx[f] + 0.5 * h * dkk[0][f]; }
+  rhs_c(nf, c2, u, k[1]);
+  rhs_jvp(nf, c2, u, du, dkk[1]);
+  for (int f = 0; f < nf; ++f) { u[f] = x[f] + 0.5 * h * k[1][f]; du[f] = dx[f] + 0.5 * h * dkk[1][f]; }
+  rhs_c(nf, c2, u, k[2]);
+  rhs_jvp(nf, c2, u, du, dkk[2]);
+  for (int f = 0; f < nf; ++f) { u[f] = x[f] + h * k[2][f]; du[f] = dx[f] + h * dkk[2][f]; }
+  rhs_c(nf, c3, u, k[3]);
+  rhs_jvp(nf, c3, u, du, dkk[3]);
+  for (int f = 0; f < nf; ++f) {
+    y[f] = x[f] + h / 6.0 * (k[0][f] + 2.0 * k[1][f] + 2.0 * k[2][f] + k[3][f]);
+    dy[f] = dx[f] + h / 6.0 * (dkk[0][f] + 2.0 * dkk[1][f] + 2.0 * dkk[2][f] + dkk[3][f]);
+  }
+}
+
+/* Adjoint of one RK4 step at input x: gx = (dy/dx)^T gy; sens[0..2] +=
+ * dJ/dPhi at the stage points z_a, z_a + h/2 (stages 2 and 3), z_a + h. */
+void orc_rk4_vjp_point(int nf, const double* kap, double phi_a, double dk, double h, const cplx* x,
+                       const cplx* gy, cplx* gx, double* sens) {
+  cplx c1[3], c2[3], c3[3], u[4][3], k[4][3], gk[4][3], gu[3];
+  nl_coef(nf, kap, phi_a, c1);
+  nl_coef(nf, kap, phi_a + dk * 0.5 * h, c2);
+  nl_coef(nf, kap, phi_a + dk * h, c3);
+  for (int f = 0; f < nf; ++f) u[0][f] = x[f];
+  rhs_c(nf, c1, u[0], k[0]);
+  for (int f = 0; f < nf; ++f) u[1][f] = x[f] + 0.5 * h * k[0][f];
+  rhs_c(nf, c2, u[1], k[1]);
+  for (int f = 0; f < nf; ++f) u[2][f] = x[f] + 0.5 * h * k[1][f];
+  rhs_c(nf, c2, u[2], k[2]);
+  for (int f = 0; f < nf; ++f) u[3][f] = x[f] + h * k[2][f];
+  rhs_c(nf, c3, u[3], k[3]);
+  /* y = x + h/6 (k1 + 2 k2 + 2 k3 + k4) */
+  for (int f = 0; f < nf; ++f) {
+    gx[f] = gy[f];
+    gk[0][f] = h / 6.0 * gy[f];
+    gk[1][f] = h / 3.0 * gy[f];
+    gk[2][f] = h / 3.0 * gy[f];
+    gk[3][f] = h / 6.0 * gy[f];
+  }
+  /* stage 4: u4 = x + h k3 */
+  for (int f = 0; f < nf; ++f) gu[f] = 0;
+  rhs_vjp(nf, c3, u[3], gk[3], gu);
+  sens[2] += phase_sens(nf, gk[3], k[3]);
+  for (int f = 0; f < nf; ++f) { gx[f] += gu[f]; gk[2][f] += h * gu[f]; }
+  /* stage 3: u3 = x + h/2 k2 */
+  for (int f = 0; f < nf; ++f) gu[f] = 0;
+  rhs_vjp(nf, c2, u[2], gk[2], gu);
+  sens[1] += phase_sens(nf, gk[2], k[2]);
+  for (int f = 0; f < nf; ++f) { gx[f] += gu[f]; gk[1][f] += 0.5 * h * gu[f]; }
+  /* stage 2: u2 = x + h/2 k1 */
+  for (int f = 0; f < nf; ++f) gu[f] = 0;
+  rhs_vjp(nf, c2, u[1], gk[1], gu);
+  sens[1] += phase_sens(nf, gk[1], k[1]);
+  for (int f = 0; f < nf; ++f) { gx[f] += gu[f]; gk[0][f] += 0.5 * h * gu[f]; }
+  /* stage 1: u1 = x */
+  for (int f = 0; f < nf; ++f) gu[f] = 0;
+  rhs_vjp(nf, c1, u[0], gk[0], gu);
+  sens[0] += phase_sens(nf, gk[0], k[0]);
+  for (int f = 0; f < nf; ++f) gx[f] += gu[f];
+}
+
+/* Adjoint of the linear step: A <- IDFT3( conj(P) DFT3(A) ). */
+void orc_linear_step_adjoint(const orc_problem* pb, cplx* fields, double dz) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  for (int f = 0; f < pb->nf; ++f) {
+    cplx* a = fields + f * n;
+    orc_fft3(a, pb->nx, pb->ny, pb->nt, -1);
+    for (int64_t idx = 0; idx < n; ++idx) {
+      int x = (int)(idx % pb->nx);
+      int y = (int)((idx / pb->nx) % pb->ny);
+      int t = (int)(idx / ((int64_t)pb->nx * pb->ny));
+      double kx = orc_angular_freq(x, pb->nx, pb->dx);
+      double ky = orc_angular_freq(y, pb->ny, pb->dy);
+      double om = orc_angular_freq(t, pb->nt, pb->dt);
+      a[idx] *= conj(cexp(dz * orc_linear_exponent(&pb->f[f], kx, ky, om)));
+    }
+    orc_fft3(a, pb->nx, pb->ny, pb->nt, +1);
+    for (int64_t i = 0; i < n; ++i) a[i] /= (double)n;
+  }
+}
+
+/* Spectral phase on one field: A <- IDFT_tau( e^{i phi(Omega)} DFT_tau A ),
+ * phi given in centred order: phi[p] belongs to Omega = 2 pi (p - NT/2)/T. */
+void orc_spectral_phase(const orc_problem* pb, cplx* a, const double* phi, int sign) {
+  int nt = pb->nt;
+  int64_t plane = (int64_t)pb->nx * pb->ny;
+  cplx* buf = (cplx*)malloc(sizeof(cplx) * nt);
+  for (int64_t q = 0; q < plane; ++q) {
+    for (int t = 0; t < nt; ++t) buf[t] = a[t * plane + q];
+    orc_fft1d(buf, nt, -1);
+    for (int m = 0; m < nt; ++m) {
+      int p = (m + nt / 2) % nt; /* centred index of bin m */
+      buf[m] *= cexp(I * sign * phi[p]);
+    }
+    orc_fft1d(buf, nt, +1);
+    for (int t = 0; t < nt; ++t) a[t * plane + q] = buf[t] / (double)nt;
+  }
+  free(buf);
+}
+
+typedef struct {
+  const orc_problem* pb;
+  const cplx* x; /* forward state at the start of the half step */
+  cplx* g;       /* adjoint in/out */
+  double kap[3];
+  double phi_a, dk, h;
+  double* part;  /* [slot][3] partial stage sensitivities */
+  int64_t chunk; /* points per slot (fixed, so the sums do not depend on threads) */
+} vjp_job;
+
+static void vjp_slots(void* p, int64_t s0, int64_t s1) {
+  vjp_job* j = (vjp_job*)p;
+  int64_t n = (int64_t)j->pb->nx * j->pb->ny * j->pb->nt;
+  int nf = j->pb->nf;
+  for (int64_t s = s0; s < s1; ++s) {
+    double acc[3] = {0, 0, 0};
+    int64_t b = s * j->chunk, e = b + j->chunk;
+    if (e > n) e = n;
+    for (int64_t i = b; i < e; ++i) {
+      cplx x[3], gy[3], gx[3];
+      for (int f = 0; f < nf; ++f) {
+        x[f] = j->x[f * n + i];
+        gy[f] = j->g[f * n + i];
+      }
+      orc_rk4_vjp_point(nf, j->kap, j->phi_a, j->dk, j->h, x, gy, gx, acc);
+      for (int f = 0; f < nf; ++f) j->g[f * n + i] = gx[f];
+    }
+    for (int k = 0; k < 3; ++k) j->part[s * 3 + k] = acc[k];
+  }
+}
+
+/* g <- adjoint of N(h) (RK4 from phi_a over h) at the forward input x;
+ * sens[0..2] = dJ/dPhi at the three stage points (start, middle, end). */
+void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, double phi_a, double dk, double h,
+                                double* sens) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  const int64_t chunk = 4096;
+  int64_t slots = (n + chunk - 1) / chunk;
+  double* part = (double*)calloc(3 * (size_t)slots, sizeof(double));
+  vjp_job j;
+  j.pb = pb;
+  j.x = x;
+  j.g = g;
+  for (int f = 0; f < pb->nf; ++f) j.kap[f] = orc_kappa(pb, f);
+  j.phi_a = phi_a;
+  j.dk = dk;
+  j.h = h;
+  j.part = part;
+  j.chunk = chunk;
+  parallel_for(slots, vjp_slots, &j);
+  sens[0] = sens[1] = sens[2] = 0.0;
+  for (int64_t s = 0; s < slots; ++s)
+    for (int k = 0; k < 3; ++k) sens[k] += part[s * 3 + k];
+  free(part);
+}
+
+/* Gradient of J = sum_f w[f] sum |A_f(L)|^2 with respect to the spectral phase
+ * phi (applied to field phi_field at z = 0, centred order, nt entries; NULL
+ * for none) and to the per-step mismatch dk_steps[0..nz-1].  Forward states
+ * of every step are kept (the oracle is for small grids).  Returns J. */
+double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                            const double* phi, int phi_field, const double* w, double* grad_phi,
+                            double* grad_dk) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  int nf = pb->nf;
+  int64_t sz = n * nf;
+  cplx* st = (cplx*)malloc(sizeof(cplx) * sz * (size_t)(nz + 1)); /* A_0 .. A_nz */
+  memcpy(st, fields_in, sizeof(cplx) * sz);
+  if (phi) orc_spectral_phase(pb, st + phi_field * n, phi, +1);
+  double* phis = (double*)malloc(sizeof(double) * (nz + 1)); /* Phi(z_j) */
+  phis[0] = 0.0;
+  for (int j = 0; j < nz; ++j) {
+    memcpy(st + (j + 1) * sz, st + j * sz, sizeof(cplx) * sz);
+    double ph = phis[j];
+    orc_propagate(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph);
+    phis[j + 1] = ph;
+  }
+  /* objective and its gradient at z = L */
+  const cplx* af = st + nz * sz;
+  double J = 0.0;
+  cplx* g = (cplx*)malloc(sizeof(cplx) * sz);
+  for (int f = 0; f < nf; ++f)
+    for (int64_t i = 0; i < n; ++i) {
+      cplx a = af[f * n + i];
+      J += w[f] * (creal(a) * creal(a) + cimag(a) * cimag(a));
+      g[f * n + i] = 2.0 * w[f] * a;
+    }
+  /* reverse sweep */
+  double* S = (double*)calloc((size_t)nz * 6, sizeof(double)); /* per step: A stages 0..2, B stages 0..2 */
+  cplx* a2 = (cplx*)malloc(sizeof(cplx) * sz);
+  for (int j = nz - 1; j >= 0; --j) {
+    const cplx* aj = st + j * sz;
+    double dk = dk_steps[j];
+    /* a2 = L(N_A(A_j)) */
+    memcpy(a2, aj, sizeof(cplx) * sz);
+    orc_nonlinear_step(pb, a2, phis[j], dk, 0.5 * dz);
+    orc_linear_step(pb, a2, dz);
+    orc_nonlinear_step_adjoint(pb, a2, g, phis[j] + dk * 0.5 * dz, dk, 0.5 * dz, S + j * 6 + 3);
+    orc_linear_step_adjoint(pb, g, dz);
+    orc_nonlinear_step_adjoint(pb, aj, g, phis[j], dk, 0.5 * dz, S + j * 6);
+  }
+  /* dJ/d dk_j: stage offsets within step j, plus dz for every later stage */
+  if (grad_dk) {
+    const double offA[3] = {0.0, 0.25 * dz, 0.5 * dz};
+    const double offB[3] = {0.5 * dz, 0.75 * dz, dz};
+    double later = 0.0;
+    for (int j = nz - 1; j >= 0; --j) {
+      double v = dz * later;
+      double tot = 0.0;
+      for (int s = 0; s < 3; ++s) {
+        v += S[j * 6 + s] * offA[s] + S[j * 6 + 3 + s] * offB[s];
+        tot += S[j * 6 + s] + S[j * 6 + 3 + s];
+      }
+      grad_dk[j] = v;
+      later += tot;
+    }
+  }
+  /* dJ/dphi_p = -(1/NT) Im sum_{x,y} conj(G^_m) A^'_m, m the bin of centred index p */
+  if (grad_phi && phi) {
+    int nt = pb->nt;
+    int64_t plane = (int64_t)pb->nx * pb->ny;
+    cplx* gb = (cplx*)malloc(sizeof(cplx) * nt);
+    cplx* ab = (cplx*)malloc(sizeof(cplx) * nt);
+    double* acc = (double*)calloc(nt, sizeof(double));
+    const cplx* a0 = st + phi_field * n;
+    const cplx* g0 = g + phi_field * n;
+    for (int64_t q = 0; q < plane; ++q) {
+      for (int t = 0; t < nt; ++t) {
+        gb[t] = g0[t * plane + q];
+        ab[t] = a0[t * plane + q];
+      }
+      orc_fft1d(gb, nt, -1);
+      orc_fft1d(ab, nt, -1);
+      for (int m = 0; m < nt; ++m) acc[m] += cimag(conj(gb[m]) * ab[m]);
+    }
+    for (int m = 0; m < nt; ++m) grad_phi[(m + nt / 2) % nt] = -acc[m] / (double)nt;
+    free(gb);
+    free(ab);
+    free(acc);
+  }
+  free(a2);
+  free(S);
+  free(g);
+  free(phis);
+  free(st);
+  return J;
+}
+
+/* J only (for finite differences): the same forward map as above. */
+double orc_objective(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                     const double* phi, int phi_field, const double* w) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  int nf = pb->nf;
+  cplx* a = (cplx*)malloc(sizeof(cplx) * n * nf);
+  memcpy(a, fields_in, sizeof(cplx) * n * nf);
+  if (phi) orc_spectral_phase(pb, a + phi_field * n, phi, +1);
+  double ph = 0.0;
+  orc_propagate(pb, a, nz, dz, dk_steps, &ph);
+  double J = 0.0;
+  for (int f = 0; f < nf; ++f)
+    for (int64_t i = 0; i < n; ++i) J += w[f] * (creal(a[f * n + i]) * creal(a[f * n + i]) + cimag(a[f * n + i]) * cimag(a[f * n + i]));
+  free(a);
+  return J;
+}
