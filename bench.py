@@ -247,6 +247,50 @@ def batched_form(dev, reps=2):
             "workload": "64 SHG runs, grids {64^2x128, 96^2x192, 128^2x256}, 200-800 steps, 2 fields"}
 
 
+def adjoint_form(dev):
+    """SHG efficiency gradient on 128x128x256 over 400 steps (256-entry spectral
+    phase, 400-entry mismatch profile), sqrt(nz) checkpointing: the time of the
+    checkpointed forward plus the reverse sweep, against the plain forward of
+    the same propagation.  CUDA events on the solver stream."""
+    import torch
+
+    import paper_2609_08384_gb300 as br
+    from paper_2609_08384_gb300 import workloads as wl
+
+    p = wl.problem_adjoint()
+    a0 = wl.peak_amplitude(1e13, wl.N_F)
+    F = wl.focused_pulse(p.grid, p.fields[1], a0, 50 * wl.UM, 200 * wl.FS, p.length).astype(np.complex64)
+    dev_in = [torch.zeros_like(torch.from_numpy(F)).to(dev), torch.from_numpy(F).to(dev)]
+    w = br.shg_efficiency_weights(p.fields, F.astype(np.complex128))
+    stream = torch.cuda.Stream(device=dev)
+    s = br.Solver(p.grid, p.fields, p.d_eff, 0.0, stream=stream, device=dev)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase)
+    s.adjoint_backward(1.0)
+    torch.cuda.synchronize(dev)
+    e[0].record(stream)
+    J = s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase)
+    e[1].record(stream)
+    s.adjoint_backward(1.0)
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    s.set_dk_profile(p.dk_profile)
+    s.set_fields(dev_in)
+    torch.cuda.synchronize(dev)
+    e[3].record(stream)
+    s.propagate(p.nz, p.dz)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_fwd, ms_bwd, ms_plain = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[3].elapsed_time(e0)
+    s.close()
+    units = float(p.grid.npoints * 2 * p.nz)
+    return {"value": units / ((ms_fwd + ms_bwd) / 1e3), "unit": UNIT, "eta": J,
+            "ms_forward_checkpointed": ms_fwd, "ms_backward": ms_bwd, "ms_plain_forward": ms_plain,
+            "gradient_cost_vs_plain_forward": (ms_fwd + ms_bwd) / ms_plain,
+            "workload": "SHG 128x128x256, 400 steps of 5 um, d eta / d(phi[256], dk[400])"}
+
+
 def run_reference(args):
     world, rank, local, dist = _dist_init(args.gpus)
     if rank != 0:
@@ -372,6 +416,7 @@ def run_ours(args):
     forms = {"plain": value}
     if not args.no_forms:
         forms["batched"] = batched_form(dev)
+        forms["adjoint"] = adjoint_form(dev)
 
     if rank != 0:
         return 0

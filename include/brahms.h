@@ -127,6 +127,35 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
 long long brahms_launch_count(const brahms_ctx* ctx);
 
 /* ------------------------------------------------------------------------
+ * Adjoint: gradients of J = sum_f w_f sum_points |A_f(L)|^2 (e.g. the SHG
+ * efficiency with w_SH = n_SH / (n_F sum |A_F(0)|^2), w_F = 0) with respect to
+ * a spectral phase phi applied at z = 0 to one field,
+ *   A <- IDFT_tau( e^{i phi(Omega)} DFT_tau A ),  phi in centred order
+ *   (phi[p] belongs to Omega = 2 pi (p - nt/2) / (nt dt)),
+ * and to the per-step mismatch profile dk[0..nz-1].  The gradient is the
+ * exact adjoint of the discrete propagation (the paper has no adjoint):
+ * the linear step reversed as IDFT3(conj(P) DFT3), each RK4 half step in
+ * reverse mode with its stages recomputed, and the mismatch through the RK4
+ * stage phases Phi(z) = Phi_j + dk_j (z - z_j).  Memory: the forward keeps a
+ * checkpoint every K steps (K = ceil(sqrt(nz)) when checkpoint_interval <= 0)
+ * and the backward recomputes K step states per segment; the library
+ * allocates (ceil(nz/K) + K + 2) field states plus small tables for it.
+ * ---------------------------------------------------------------------- */
+
+/* Set the fields (as brahms_set_fields), apply the phase (phi may be NULL),
+ * propagate nz steps of dz with the profile dk, keep checkpoints, and return
+ * J (weights: nfields entries).  Leaves the fields at z = nz dz.  Waits. */
+brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields, int dtype, int on_device,
+                                     const double* phi, int phi_field, const double* dk, int nz, double dz,
+                                     const double* weights, int checkpoint_interval, double* J);
+
+/* Reverse sweep for the last brahms_adjoint_forward: writes gscale * dJ/dphi
+ * (nt entries, centred order; zeros if no phase was applied) and
+ * gscale * dJ/d dk_j (nz entries); either pointer may be NULL.  Leaves the
+ * context state undefined (call brahms_set_fields before propagating). */
+brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* grad_phi, double* grad_dk);
+
+/* ------------------------------------------------------------------------
  * Batched form (two-field SHG sweeps): many independent simulations of
  * uneven grids, mismatch and crystal length advanced by one persistent
  * cooperative kernel whose launch is captured in a CUDA graph.  Each instance

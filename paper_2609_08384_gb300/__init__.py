@@ -60,6 +60,9 @@ SIGNATURES = {
     "brahms_launch_count": (_c.c_longlong, [_vp]),
     "brahms_energy_static": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double,
                                         _c.c_double, _c.c_double, _c.POINTER(FieldParams), _vp, _vp]),
+    "brahms_adjoint_forward": (_c.c_int, [_vp, _c.POINTER(_vp), _c.c_int, _c.c_int, _dp, _c.c_int, _dp, _c.c_int,
+                                          _c.c_double, _dp, _c.c_int, _dp]),
+    "brahms_adjoint_backward": (_c.c_int, [_vp, _c.c_double, _dp, _dp]),
     "brahms_batch_create": (_c.c_int, [_c.POINTER(_vp), _vp]),
     "brahms_batch_add": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double,
                                     _c.POINTER(FieldParams), _c.c_double, _c.c_double, _c.c_int, _c.c_double,
@@ -231,6 +234,30 @@ class Solver:
     def launch_count(self) -> int:
         return int(load().brahms_launch_count(self.ctx))
 
+    def adjoint_forward(self, fields, dk, nz, dz, weights, phi=None, phi_field=1, checkpoint_interval=0):
+        """J = sum_f w_f sum |A_f(L)|^2 after the phase phi (centred order) and
+        nz steps with the mismatch profile dk; keeps checkpoints."""
+        ptrs, dtype, dev = self._marshal(fields, None)
+        dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (int(nz),)))
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+        J = ctypes.c_double()
+        _check(self.ctx, load().brahms_adjoint_forward(
+            self.ctx, _ptr_array(ptrs), dtype, int(dev), None if ph is None else ph.ctypes.data_as(_dp),
+            int(phi_field), dks.ctypes.data_as(_dp), int(nz), float(dz), w.ctypes.data_as(_dp),
+            int(checkpoint_interval), ctypes.byref(J)))
+        self._adj = (int(nz), ph is not None)
+        return J.value
+
+    def adjoint_backward(self, gscale=1.0):
+        """(gscale dJ/dphi or None, gscale dJ/d dk) for the last adjoint_forward."""
+        nz, has_phi = self._adj
+        gphi = np.zeros(self.grid.nt)
+        gdk = np.zeros(nz)
+        _check(self.ctx, load().brahms_adjoint_backward(self.ctx, float(gscale), gphi.ctypes.data_as(_dp),
+                                                        gdk.ctypes.data_as(_dp)))
+        return (gphi if has_phi else None), gdk
+
     # -- helpers
     def _marshal(self, arrs, on_device, writable=False):
         import torch
@@ -366,3 +393,37 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def shg_efficiency_weights(fields, input_f):
+    """Weights that make J the SHG efficiency E_SH(L)/E_F(0) for fields
+    (SH, F): w_SH = n_SH / (n_F sum |A_F(0)|^2), w_F = 0 (the common factor
+    1/2 c eps0 dx dy dtau cancels; the spectral phase keeps E_F(0))."""
+    s = float(np.sum(np.abs(np.asarray(input_f, dtype=np.complex128)) ** 2))
+    return np.array([fields[0].n / (fields[1].n * s), 0.0])
+
+
+def shg_efficiency_function():
+    """torch.autograd.Function: eta(phi, dk) for a Solver of SHG fields.
+
+    forward(phi, dk, solver, fields, nz, dz, weights, interval) runs the
+    checkpointed forward through brahms_adjoint_forward and returns eta as a
+    float64 tensor; backward calls brahms_adjoint_backward with the incoming
+    gradient as gscale and returns gradients for phi and dk (CPU float64)."""
+    import torch
+
+    class _Eta(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, phi, dk, solver, fields, nz, dz, weights, interval):
+            J = solver.adjoint_forward(fields, dk.detach().cpu().numpy(), nz, dz, weights,
+                                       phi=phi.detach().cpu().numpy(), phi_field=1,
+                                       checkpoint_interval=interval)
+            ctx.solver = solver
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, g):
+            gphi, gdk = ctx.solver.adjoint_backward(float(g))
+            return (torch.from_numpy(gphi), torch.from_numpy(gdk), None, None, None, None, None, None)
+
+    return _Eta

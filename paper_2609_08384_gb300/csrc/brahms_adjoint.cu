@@ -1,0 +1,268 @@
+// Adjoint of the split-step propagation with sqrt(nz) checkpointing:
+// gradients of J = sum_f w_f sum |A_f(L)|^2 with respect to an input spectral
+// phase and to the per-step mismatch profile.
+//
+// Forward: the state is checkpointed every K steps (K = ceil(sqrt(nz)) by
+// default) while the fused propagation runs.  Backward: segments are visited
+// last to first; each is recomputed from its checkpoint one step at a time
+// (keeping the K step states), then reversed step by step:
+//   a2 = L(N_A(A_j))                (recomputed)
+//   G <- N_B^T(a2) G                (RK4 reverse mode, stage phase sensitivities)
+//   G <- IDFT3( conj(P) DFT3(G) )   (adjoint of the linear step)
+//   G <- N_A^T(A_j) G
+// The mismatch gradient follows from the stage sensitivities dJ/dPhi with
+// Phi(z) = Phi_j + dk_j (z - z_j); the phase gradient from the tau-spectra of
+// the adjoint and of the phased input.
+#include <algorithm>
+
+#include "ctx_internal.h"
+
+using namespace brahms_host;
+
+namespace {
+
+constexpr int kVjpBlocks = 152 * 4;
+
+brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
+  const size_t state = sizeof(float2) * (size_t)ctx->nf * (size_t)ctx->npoints();
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += align256(b);
+    return o;
+  };
+  const size_t o_ck = take(state * nseg), o_seg = take(state * K), o_w = take(state), o_g = take(state);
+  const size_t o_tab = take(sizeof(float2) * (ctx->nx + ctx->ny + ctx->nt));
+  const size_t o_phi = take(sizeof(double) * ctx->nt), o_acc = take(sizeof(double) * ctx->nt);
+  const size_t o_part = take(sizeof(double) * (size_t)nz * 2 * kVjpBlocks * 3);
+  const size_t o_sens = take(sizeof(double) * (size_t)nz * 6);
+  if (off > ctx->adj_bytes) {
+    if (ctx->adj_mem) cudaFree(ctx->adj_mem);
+    ctx->adj_mem = nullptr;
+    ctx->adj_bytes = 0;
+    if (cudaMalloc((void**)&ctx->adj_mem, off) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, BRAHMS_E_OOM, "adjoint checkpoint memory");
+    }
+    ctx->adj_bytes = off;
+  }
+  char* m = ctx->adj_mem;
+  ctx->adj_ckpt = (float2*)(m + o_ck);
+  ctx->adj_seg = (float2*)(m + o_seg);
+  ctx->adj_work = (float2*)(m + o_w);
+  ctx->adj_g = (float2*)(m + o_g);
+  ctx->adj_tab = (float2*)(m + o_tab);
+  ctx->adj_phi_dev = (double*)(m + o_phi);
+  ctx->adj_acc = (double*)(m + o_acc);
+  ctx->adj_part = (double*)(m + o_part);
+  ctx->adj_sens = (double*)(m + o_sens);
+  return BRAHMS_OK;
+}
+
+// One linear step (forward or adjoint) on `data`, real space in and out.
+brahms_status linear_on(brahms_ctx* ctx, float2* data, double dz, bool adjoint) {
+  const int nx = ctx->nx, ny = ctx->ny, nt = ctx->nt, nf = ctx->nf;
+  brahms::XPassArgs xf = xargs(ctx, brahms::XM_FWD, dz), xi = xargs(ctx, brahms::XM_INV, dz);
+  xf.data = data;
+  xi.data = data;
+  xi.scale = 1.f;  // 1/(nx ny nt) is part of the tau-pass multiplier
+  brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
+  ay.data = data;
+  at.data = data;
+  at.conj_p = adjoint ? 1 : 0;
+  brahms_status s = build_tables(ctx, dz);
+  if (s != BRAHMS_OK) return s;
+  BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xf, ctx->stream); }));
+  BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
+  BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
+  BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ay, ctx->stream); }));
+  BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xi, ctx->stream); }));
+  return BRAHMS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields, int dtype, int on_device,
+                                     const double* phi, int phi_field, const double* dk, int nz, double dz,
+                                     const double* weights, int checkpoint_interval, double* J) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
+    return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
+  if (phi && (phi_field < 0 || phi_field >= ctx->nf)) return fail(ctx, BRAHMS_E_ARG, "phi_field out of range");
+  if (phi)
+    for (int i = 0; i < ctx->nt; ++i)
+      if (!std::isfinite(phi[i])) return fail(ctx, BRAHMS_E_ARG, "phi has non-finite entries");
+  const int K = checkpoint_interval > 0 ? std::min(checkpoint_interval, nz)
+                                        : std::max(1, (int)std::ceil(std::sqrt((double)nz)));
+  const int nseg = (nz + K - 1) / K;
+  brahms_status s = adj_alloc(ctx, nz, K, nseg);
+  if (s != BRAHMS_OK) return s;
+  s = brahms_set_fields(ctx, fields, dtype, on_device);
+  if (s != BRAHMS_OK) return s;
+  s = brahms_set_dk_profile(ctx, dk, nz);
+  if (s != BRAHMS_OK) return s;
+  const long long n = ctx->npoints();
+  ctx->adj_has_phi = phi != nullptr;
+  if (phi) {
+    // A_f <- IDFT_tau( e^{i phi} DFT_tau A_f ) on the chosen field
+    BR_CK(cudaMemcpyAsync(ctx->adj_phi_dev, phi, sizeof(double) * ctx->nt, cudaMemcpyHostToDevice, ctx->stream));
+    float2* px = ctx->adj_tab;
+    float2* py = px + ctx->nx;
+    float2* pt = py + ctx->ny;
+    BR_CK(launch(ctx, 4, 1, [&] {
+      return brahms::run_phase_tables(px, ctx->nx, py, ctx->ny, pt, ctx->nt, ctx->adj_phi_dev, +1, ctx->stream);
+    }));
+    brahms::AxisArgs at = aargs(ctx, 2);
+    at.data = ctx->state + phi_field * n;
+    at.ntiles = (long long)ctx->ny * at.xtiles;
+    at.px = px;
+    at.py = py;
+    at.pt = pt;
+    const double inv = 1.0 / (double)ctx->nt;
+    at.scale = (float)inv;
+    at.scale_lo = (float)(inv - (double)at.scale);
+    BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
+  }
+  for (int seg = 0; seg < nseg; ++seg) {
+    BR_CK(cudaMemcpyAsync(ctx->adj_ckpt + (size_t)seg * ctx->nf * n, ctx->state, sizeof(float2) * ctx->nf * n,
+                          cudaMemcpyDeviceToDevice, ctx->stream));
+    s = brahms_propagate(ctx, std::min(K, nz - seg * K), dz);
+    if (s != BRAHMS_OK) return s;
+  }
+  s = finish_with_check(ctx);
+  if (s != BRAHMS_OK) return s;
+  double j = 0.0;
+  for (int f = 0; f < ctx->nf; ++f) j += weights[f] * ctx->energy_host[f];
+  if (J) *J = j;
+  // bookkeeping for the reverse sweep (Phi_j exactly as brahms_propagate accumulates it)
+  ctx->adj_nz = nz;
+  ctx->adj_K = K;
+  ctx->adj_nseg = nseg;
+  ctx->adj_dz = dz;
+  ctx->adj_phi_field = phi ? phi_field : -1;
+  ctx->adj_weights.assign(weights, weights + ctx->nf);
+  ctx->adj_dk.assign(dk, dk + nz);
+  ctx->adj_phis.assign(nz + 1, 0.0);
+  double ph = 0.0;
+  for (int i = 0; i < nz; ++i) {
+    ctx->adj_phis[i] = ph;
+    ph += dk[i] * dz;
+  }
+  ctx->adj_phis[nz] = ph;
+  ctx->adj_ready = true;
+  return BRAHMS_OK;
+}
+
+brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* grad_phi, double* grad_dk) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (!ctx->adj_ready) return fail(ctx, BRAHMS_E_STATE, "adjoint_backward before adjoint_forward");
+  if (!std::isfinite(gscale)) return fail(ctx, BRAHMS_E_ARG, "gscale is not finite");
+  const int nz = ctx->adj_nz, K = ctx->adj_K, nseg = ctx->adj_nseg, nf = ctx->nf, nx = ctx->nx;
+  const double dz = ctx->adj_dz;
+  const long long n = ctx->npoints();
+  const size_t sbytes = sizeof(float2) * nf * (size_t)n;
+  // G = 2 w_f gscale A_f(L); the final forward state is still in ctx->state
+  float sc[3] = {0.f, 0.f, 0.f};
+  for (int f = 0; f < nf; ++f) sc[f] = (float)(2.0 * ctx->adj_weights[f] * gscale);
+  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_scale_fields(ctx->state, ctx->adj_g, n, nf, n, sc, ctx->stream); }));
+  const brahms::XPassArgs base = xargs(ctx, brahms::XM_NL_FIRST, dz);
+  for (int seg = nseg - 1; seg >= 0; --seg) {
+    const int j0 = seg * K, j1 = std::min(nz, j0 + K);
+    // recompute the segment's step states A_j0 .. A_{j1-1}
+    BR_CK(cudaMemcpyAsync(ctx->state, ctx->adj_ckpt + (size_t)seg * nf * n, sbytes, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+    for (int j = j0; j < j1; ++j) {
+      BR_CK(cudaMemcpyAsync(ctx->adj_seg + (size_t)(j - j0) * nf * n, ctx->state, sbytes, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+      if (j < j1 - 1) {
+        ctx->step = j;
+        ctx->phi = ctx->adj_phis[j];
+        brahms_status s = brahms_propagate(ctx, 1, dz);
+        if (s != BRAHMS_OK) return s;
+      }
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      float2* aj = ctx->adj_seg + (size_t)(j - j0) * nf * n;
+      const double dkj = ctx->adj_dk[j], phj = ctx->adj_phis[j];
+      // a2 = L(N_A(A_j)) in the work buffer
+      BR_CK(cudaMemcpyAsync(ctx->adj_work, aj, sbytes, cudaMemcpyDeviceToDevice, ctx->stream));
+      {
+        brahms::XPassArgs xa = base;
+        xa.data = ctx->adj_work;
+        xa.phiA = phj;
+        xa.dkA = dkj;
+        BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xa, ctx->stream); }));
+        brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
+        ay.data = ctx->adj_work;
+        at.data = ctx->adj_work;
+        brahms_status s = build_tables(ctx, dz);
+        if (s != BRAHMS_OK) return s;
+        BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
+        BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
+        BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));
+        brahms::XPassArgs xi = xargs(ctx, brahms::XM_INV, dz);
+        xi.data = ctx->adj_work;
+        xi.scale = 1.f;
+        BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xi, ctx->stream); }));
+      }
+      double* partB = ctx->adj_part + ((size_t)j * 2 + 1) * kVjpBlocks * 3;
+      double* partA = ctx->adj_part + ((size_t)j * 2) * kVjpBlocks * 3;
+      BR_CK(launch(ctx, 4, 1, [&] {
+        return brahms::run_rk4_vjp(nf, ctx->adj_work, ctx->adj_g, n, n, phj + dkj * 0.5 * dz, dkj, 0.5 * dz, base.kh,
+                                   partB, kVjpBlocks, ctx->stream);
+      }));
+      brahms_status s = linear_on(ctx, ctx->adj_g, dz, true);
+      if (s != BRAHMS_OK) return s;
+      BR_CK(launch(ctx, 4, 1, [&] {
+        return brahms::run_rk4_vjp(nf, aj, ctx->adj_g, n, n, phj, dkj, 0.5 * dz, base.kh, partA, kVjpBlocks,
+                                   ctx->stream);
+      }));
+    }
+  }
+  // mismatch gradient from the stage sensitivities
+  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_sens_reduce(ctx->adj_part, kVjpBlocks, nz, ctx->adj_sens, ctx->stream); }));
+  std::vector<double> S((size_t)nz * 6);
+  BR_CK(cudaMemcpyAsync(S.data(), ctx->adj_sens, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  std::vector<double> acc;
+  if (grad_phi && ctx->adj_has_phi) {
+    // dJ/dphi_p = -(1/nt) sum_{x,y} Im(conj(G^_m) A^_m), m = (p - nt/2) mod nt
+    const int pf = ctx->adj_phi_field;
+    float2* gw = ctx->adj_work;
+    float2* aw = ctx->adj_work + n;
+    BR_CK(cudaMemcpyAsync(gw, ctx->adj_g + (size_t)pf * n, sizeof(float2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    BR_CK(cudaMemcpyAsync(aw, ctx->adj_ckpt + (size_t)pf * n, sizeof(float2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+    brahms::AxisArgs at = aargs(ctx, 2);
+    at.data = ctx->adj_work;
+    at.ntiles = 2LL * ctx->ny * at.xtiles;  // the two copies
+    BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, false, at, ctx->stream); }));
+    BR_CK(launch(ctx, 4, 1, [&] {
+      return brahms::run_phase_grad(gw, aw, (long long)ctx->nx * ctx->ny, ctx->nt, ctx->adj_acc, ctx->stream);
+    }));
+    acc.resize(ctx->nt);
+    BR_CK(cudaMemcpyAsync(acc.data(), ctx->adj_acc, sizeof(double) * ctx->nt, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  BR_CK(cudaStreamSynchronize(ctx->stream));
+  if (grad_dk) {
+    const double offA[3] = {0.0, 0.25 * dz, 0.5 * dz};
+    const double offB[3] = {0.5 * dz, 0.75 * dz, dz};
+    double later = 0.0;
+    for (int j = nz - 1; j >= 0; --j) {
+      double v = dz * later, tot = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        v += S[j * 6 + k] * offA[k] + S[j * 6 + 3 + k] * offB[k];
+        tot += S[j * 6 + k] + S[j * 6 + 3 + k];
+      }
+      grad_dk[j] = v;
+      later += tot;
+    }
+  }
+  if (grad_phi) {
+    const int nt = ctx->nt;
+    for (int m = 0; m < nt; ++m) grad_phi[(m + nt / 2) % nt] = acc.empty() ? 0.0 : -acc[m] / (double)nt;
+  }
+  return BRAHMS_OK;
+}
+
+}  // extern "C"

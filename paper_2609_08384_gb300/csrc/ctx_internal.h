@@ -1,0 +1,268 @@
+// Host-side context of the C ABI and the helpers shared by the forward
+// (brahms_api.cu) and adjoint (brahms_adjoint.cu) entry points.
+#pragma once
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "brahms.h"
+#include "kernels.cuh"
+
+namespace brahms_host {
+
+constexpr double kC0 = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kHbar = 1.054571817e-34;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kRedBlocks = 152 * 4;  // energy partials per field
+constexpr int kKinds = 5;
+
+inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+struct Layout {
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, total;
+};
+
+inline Layout make_layout(int nx, int ny, int nt, int nf) {
+  Layout L{};
+  size_t off = 0;
+  const size_t n = (size_t)nx * ny * nt;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+    return o;
+  };
+  L.state = take(sizeof(float2) * n * nf);
+  L.px = take(sizeof(float2) * nx * nf);
+  L.py = take(sizeof(float2) * ny * nf);
+  L.pt = take(sizeof(float2) * nt * nf);
+  L.twx = take(sizeof(float4) * nx);
+  L.twy = take(sizeof(float4) * ny);
+  L.twt = take(sizeof(float4) * nt);
+  L.partial = take(sizeof(double) * kRedBlocks * nf);
+  L.energy = take(sizeof(double) * nf);
+  L.total = off;
+  return L;
+}
+
+struct TimedLaunch {
+  int kind;
+  cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct brahms_ctx {
+  using Layout = brahms_host::Layout;
+  using TimedLaunch = brahms_host::TimedLaunch;
+  int nx = 0, ny = 0, nt = 0, nf = 0;
+  double dx = 0, dy = 0, dt = 0, d_eff = 0, dk = 0;
+  brahms_field_params fp[3]{};
+  cudaStream_t stream = nullptr;
+  bool own_ws = false;
+  char* ws = nullptr;
+  Layout L{};
+  float2 *state = nullptr, *px = nullptr, *py = nullptr, *pt = nullptr;
+  float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
+  double *partial = nullptr, *energy_dev = nullptr;
+  double* energy_host = nullptr;  // pinned, nf entries
+  double tab_dz = NAN;
+  bool have_fields = false;
+  double z = 0.0, phi = 0.0;
+  long long step = 0;
+  std::vector<double> dk_profile;
+  std::string err;
+  long long launches = 0;
+  // timing
+  bool timing = false;
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> event_pool;
+  double kind_ms[brahms_host::kKinds]{};
+  long long kind_n[brahms_host::kKinds]{};
+  // adjoint (allocated on first use by brahms_adjoint_forward)
+  char* adj_mem = nullptr;
+  size_t adj_bytes = 0;
+  float2* adj_ckpt = nullptr;  // checkpoints, one state each
+  float2* adj_seg = nullptr;   // states of one segment
+  float2* adj_work = nullptr;  // recomputed state within a step
+  float2* adj_g = nullptr;     // adjoint state
+  float2* adj_tab = nullptr;   // spectral-phase tables: x (nx), y (ny), tau (nt)
+  double* adj_part = nullptr;  // stage-sensitivity partials
+  double* adj_sens = nullptr;  // [nz][6] stage sensitivities
+  double* adj_phi_dev = nullptr;  // spectral phase (nt)
+  double* adj_acc = nullptr;      // phase-gradient accumulators (nt)
+  bool adj_has_phi = false;
+  int adj_nz = 0, adj_K = 0, adj_nseg = 0, adj_phi_field = -1;
+  double adj_dz = 0.0;
+  bool adj_ready = false;
+  std::vector<double> adj_weights, adj_dk, adj_phis;
+
+  long long npoints() const { return (long long)nx * ny * nt; }
+};
+
+namespace brahms_host {
+
+inline brahms_status fail(brahms_ctx* c, brahms_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+inline brahms_status cuda_fail(brahms_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(c, BRAHMS_E_CUDA, m);
+}
+
+#define BR_CK(call)                                      \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+inline cudaEvent_t take_event(brahms_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch wrapper: counts launches and, when timing is on, brackets the
+// launch with events on the context stream.
+template <class Fn>
+inline cudaError_t launch(brahms_ctx* c, int kind, int nlaunch, Fn fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (c->timing) {
+    a = take_event(c);
+    b = take_event(c);
+    if (a && b) cudaEventRecord(a, c->stream);
+  }
+  cudaError_t e = fn();
+  c->launches += nlaunch;
+  if (c->timing && a && b) {
+    cudaEventRecord(b, c->stream);
+    c->timed.push_back({kind, a, b});
+  }
+  return e;
+}
+
+inline brahms_status collect_timing(brahms_ctx* ctx) {
+  if (ctx->timed.empty()) return BRAHMS_OK;
+  BR_CK(cudaStreamSynchronize(ctx->stream));
+  for (auto& t : ctx->timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      ctx->kind_ms[t.kind] += ms;
+      ctx->kind_n[t.kind] += 1;
+    }
+    ctx->event_pool.push_back(t.a);
+    ctx->event_pool.push_back(t.b);
+  }
+  ctx->timed.clear();
+  return BRAHMS_OK;
+}
+
+inline bool finite_params(const brahms_field_params& f) {
+  return std::isfinite(f.lambda) && std::isfinite(f.n) && std::isfinite(f.delta) && std::isfinite(f.k2) &&
+         std::isfinite(f.k3) && std::isfinite(f.rho) && std::isfinite(f.alpha) && f.lambda > 0 && f.n > 0 &&
+         std::fabs(f.rho) < 1.5;
+}
+
+inline double kappa(const brahms_ctx* c, int f) { return kTwoPi * c->d_eff / (c->fp[f].n * c->fp[f].lambda); }
+
+inline brahms_status build_tables(brahms_ctx* ctx, double dz) {
+  if (ctx->tab_dz == dz) return BRAHMS_OK;
+  brahms::TableArgs a{};
+  a.px = ctx->px;
+  a.py = ctx->py;
+  a.pt = ctx->pt;
+  a.nx = ctx->nx;
+  a.ny = ctx->ny;
+  a.nt = ctx->nt;
+  a.nf = ctx->nf;
+  a.dx = ctx->dx;
+  a.dy = ctx->dy;
+  a.dt = ctx->dt;
+  a.dz = dz;
+  for (int f = 0; f < ctx->nf; ++f) {
+    a.k[f] = kTwoPi * ctx->fp[f].n / ctx->fp[f].lambda;
+    a.rho[f] = ctx->fp[f].rho;
+    a.delta[f] = ctx->fp[f].delta;
+    a.k2[f] = ctx->fp[f].k2;
+    a.k3[f] = ctx->fp[f].k3;
+    a.alpha[f] = ctx->fp[f].alpha;
+  }
+  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_prop_tables(a, ctx->stream); }));
+  ctx->tab_dz = dz;
+  return BRAHMS_OK;
+}
+
+inline brahms::XPassArgs xargs(brahms_ctx* c, int mode, double dz) {
+  brahms::XPassArgs a{};
+  a.data = c->state;
+  a.fstride = c->npoints();
+  a.rows = (long long)c->ny * c->nt;
+  a.tw = c->twx;
+  a.mode = mode;
+  a.dz = dz;
+  for (int f = 0; f < c->nf; ++f) {
+    double k = kappa(c, f);
+    if (c->nf == 2 && f == 0) k *= 0.5;  // degenerate SHG: 1/2 on the SH equation
+    a.kh[f] = (float)(k * 0.5 * dz);
+  }
+  a.scale = 1.f;
+  return a;
+}
+
+inline brahms::AxisArgs aargs(brahms_ctx* c, int axis) {
+  brahms::AxisArgs a{};
+  a.data = c->state;
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.nt = c->nt;
+  a.fstride = c->npoints();
+  const int n = axis == 1 ? c->ny : c->nt;
+  const int tx = brahms::col_tile_of(n);
+  a.xtiles = (c->nx + tx - 1) / tx;
+  a.ntiles = (long long)c->nf * (axis == 1 ? c->nt : c->ny) * a.xtiles;
+  a.tw = axis == 1 ? c->twy : c->twt;
+  a.px = c->px;
+  a.py = c->py;
+  a.pt = c->pt;
+  const double inv_n = 1.0 / (double)c->npoints();
+  a.scale = (float)inv_n;
+  a.scale_lo = (float)(inv_n - (double)a.scale);
+  return a;
+}
+
+inline double dk_of_step(const brahms_ctx* c, long long j) {
+  return j < (long long)c->dk_profile.size() ? c->dk_profile[(size_t)j] : c->dk;
+}
+
+// Enqueue an FP64 |A|^2 reduction per field into energy_host (pinned).
+inline brahms_status enqueue_energy(brahms_ctx* ctx) {
+  BR_CK(launch(ctx, 4, 2, [&] {
+    return brahms::run_energy(ctx->state, ctx->npoints(), ctx->nf, ctx->npoints(), ctx->partial, kRedBlocks,
+                              ctx->energy_dev, ctx->stream);
+  }));
+  BR_CK(cudaMemcpyAsync(ctx->energy_host, ctx->energy_dev, sizeof(double) * ctx->nf, cudaMemcpyDeviceToHost,
+                        ctx->stream));
+  return BRAHMS_OK;
+}
+
+inline brahms_status finish_with_check(brahms_ctx* ctx) {
+  brahms_status s = enqueue_energy(ctx);
+  if (s != BRAHMS_OK) return s;
+  BR_CK(cudaStreamSynchronize(ctx->stream));
+  for (int f = 0; f < ctx->nf; ++f)
+    if (!std::isfinite(ctx->energy_host[f]))
+      return fail(ctx, BRAHMS_E_NONFINITE, "fields are not finite (dz too large for the coupling, Sec. 3.2)");
+  return BRAHMS_OK;
+}
+
+}  // namespace

@@ -48,6 +48,7 @@ struct AxisArgs {
   const float2* py;    // [nf][ny]
   const float2* pt;    // [nf][nt]
   float scale, scale_lo;  // 1/(nx ny nt) = scale + scale_lo (lo = 0 for powers of two)
+  int conj_p;             // apply conj(P) (the adjoint of the linear step)
 };
 
 // ------------------------------------------------------------ tile shapes
@@ -361,13 +362,16 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
     const float2 dx = p.px[a.f * p.nx + a.x], dy = p.py[a.f * p.ny + a.other];
     dxy = cadd(cadd(dx, dy), cmul(dx, dy));
   }
+  if (p.conj_p) dxy.y = -dxy.y;
   const float2* pt = p.pt + (a.act ? a.f * p.nt : 0);
+  const float tsign = p.conj_p ? -1.f : 1.f;
 #pragma unroll
   for (int b = 0; b < E / RL; ++b)
 #pragma unroll
     for (int r = 0; r < RL; ++r) {
       const int k = t + b * T + r * SL;
-      const float2 dt = pt[k];
+      float2 dt = pt[k];
+      dt.y *= tsign;
       const float2 d = cadd(cadd(dxy, dt), cmul(dxy, dt));
       float2 w = v[b * RL + r];
       w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
@@ -430,6 +434,16 @@ cudaError_t run_energy(const float2* data, long long n, int nf, long long fstrid
                        int nblocks, double* out, cudaStream_t s);
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
 cudaError_t run_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t s);
+
+// adjoint kernels (k_adjoint.cu)
+cudaError_t run_rk4_vjp(int nf, const float2* x, float2* g, long long n, long long fstride, double phi_a, double dk,
+                        double h, const float* kh, double* partial, int nblocks, cudaStream_t s);
+cudaError_t run_scale_fields(const float2* a, float2* g, long long n, int nf, long long fstride, const float* s,
+                             cudaStream_t st);
+cudaError_t run_phase_grad(const float2* gh, const float2* ah, long long plane, int nt, double* acc, cudaStream_t s);
+cudaError_t run_sens_reduce(const double* partial, int nblocks, int nz, double* sens, cudaStream_t s);
+cudaError_t run_phase_tables(float2* px, int nx, float2* py, int ny, float2* pt, int nt, const double* phi, int sign,
+                             cudaStream_t s);
 
 }  // namespace brahms
 

@@ -1,0 +1,153 @@
+"""GPU adjoint (checkpointed reverse sweep) against the FP64 oracle gradient,
+finite differences of the GPU forward, and through torch.autograd."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2609_08384_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3  # relative L2 over the whole gradient vector
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2609_08384_gb300 import build
+    build.build()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def _shg_case(n, nt, nz, dz, seed, intensity=3e13):
+    g = wl.Grid(n, n, nt, 12.5 * wl.UM, 12.5 * wl.UM, 50 * wl.FS)
+    f = wl.shg_fields()
+    a0 = wl.peak_amplitude(intensity, wl.N_F)
+    F = wl.focused_pulse(g, f[1], a0, 4 * n / 32 * 25 * wl.UM, 8 * nt / 64 * 50 * wl.FS, nz * dz)
+    ins = [np.zeros_like(F).astype(np.complex64), F.astype(np.complex64)]
+    rng = np.random.default_rng(wl.SEED_BASE + seed)
+    phi = rng.normal(0, 0.1, nt)
+    dk = rng.normal(0, 0.1, nz) / wl.MM
+    return g, f, ins, phi, dk
+
+
+def _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, phi_field=1):
+    import paper_2609_08384_gb300 as br
+    s = br.Solver(g, f, wl.D_EFF, 0.0)
+    J = s.adjoint_forward([torch.from_numpy(a).cuda() for a in ins], dk, nz, dz, w, phi=phi, phi_field=phi_field,
+                          checkpoint_interval=interval)
+    gphi, gdk = s.adjoint_backward(1.0)
+    s.close()
+    return J, gphi, gdk
+
+
+@pytest.mark.parametrize("n,nt,nz", [(32, 64, 60), (64, 128, 24)])
+def test_shg_gradient_matches_oracle(n, nt, nz):
+    dz = 5 * wl.UM * (400 / nz) * 0.25
+    g, f, ins, phi, dk = _shg_case(n, nt, nz, dz, 50 + n)
+    w = np.array([f[0].n / (f[1].n * float(np.sum(np.abs(ins[1].astype(np.complex128)) ** 2))), 0.0])
+    J, gphi, gdk = _gpu_grad(g, f, ins, phi, dk, nz, dz, w)
+    prob = oracle.make_problem(g, f, wl.D_EFF)
+    Jr, gphi_r, gdk_r = oracle.adjoint_gradient(prob, [a.astype(np.complex128) for a in ins], nz, dz, dk, w,
+                                                phi=phi, phi_field=1)
+    assert Jr > 1e-3
+    assert abs(J / Jr - 1) < 1e-4
+    assert rel_l2(gphi, gphi_r) < GRAD_TOL
+    assert rel_l2(gdk, gdk_r) < GRAD_TOL
+
+
+def test_three_field_gradient_matches_oracle():
+    g = wl.Grid(24, 16, 32, 6 * wl.UM, 6 * wl.UM, 30 * wl.FS)
+    fields = [wl.FieldParams(wl.LAM_P, wl.N_P, delta=1e-10, k2=2e-25, rho=2e-3),
+              wl.FieldParams(wl.LAM_S, wl.N_S, k2=1e-25),
+              wl.FieldParams(wl.LAM_I, wl.N_I, delta=-1e-10, k2=5e-26, rho=1e-3, alpha=20.0)]
+    x, y, t = g.axes()
+    env = np.exp(-(x[None, None] ** 2 + y[None, :, None] ** 2) / (25 * wl.UM) ** 2 - (t[:, None, None] / (150 * wl.FS)) ** 2)
+    rng = np.random.default_rng(7)
+    ins = [(8e7 * env).astype(np.complex64), (2e7 * env * np.exp(0.3j)).astype(np.complex64),
+           (1e6 * rng.standard_normal(env.shape)).astype(np.complex64)]
+    nz, dz = 16, 25 * wl.UM
+    dk = rng.normal(300.0, 200.0, nz)
+    phi = rng.normal(0, 0.2, g.nt)
+    w = np.array([0.0, 1e-15, 5e-16])
+    J, gphi, gdk = _gpu_grad(g, fields, ins, phi, dk, nz, dz, w, phi_field=0)
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    Jr, gphi_r, gdk_r = oracle.adjoint_gradient(prob, [a.astype(np.complex128) for a in ins], nz, dz, dk, w,
+                                                phi=phi, phi_field=0)
+    assert abs(J / Jr - 1) < 1e-4
+    assert rel_l2(gphi, gphi_r) < GRAD_TOL
+    assert rel_l2(gdk, gdk_r) < GRAD_TOL
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    nz, dz = 30, 20 * wl.UM
+    g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 60)
+    w = np.array([1e-20, 0.0])
+    res = [_gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=k) for k in (0, 7, nz, 1)]
+    for J, gp, gd in res[1:]:
+        assert J == res[0][0]
+        assert np.array_equal(gp, res[0][1]) and np.array_equal(gd, res[0][2])
+
+
+def test_adjoint_gradient_full_size_directional_derivative():
+    """SHG efficiency on 128x128x256 over 400 steps of 5 um, with respect to
+    the 256-entry spectral phase and the 400-entry mismatch profile: the
+    adjoint's directional derivative along the gradient matches a central
+    difference of the GPU forward."""
+    import paper_2609_08384_gb300 as br
+    p = wl.problem_adjoint()
+    f = p.fields
+    a0 = wl.peak_amplitude(1e13, wl.N_F)
+    F = wl.focused_pulse(p.grid, f[1], a0, 50 * wl.UM, 200 * wl.FS, p.length).astype(np.complex64)
+    ins = [np.zeros_like(F), F]
+    phi, dk = p.spectral_phase, p.dk_profile
+    w = br.shg_efficiency_weights(f, F.astype(np.complex128))
+    s = br.Solver(p.grid, f, p.d_eff, 0.0)
+    dev = [torch.from_numpy(a).cuda() for a in ins]
+    J = s.adjoint_forward(dev, dk, p.nz, p.dz, w, phi=phi)
+    gphi, gdk = s.adjoint_backward(1.0)
+    assert 0.01 < J < 1.0
+    # scale mismatch steps to the unit of the draw (1/mm) so both blocks count
+    d_phi, d_dk = gphi, gdk * (1.0 / wl.MM)
+    norm = np.sqrt(np.sum(d_phi ** 2) + np.sum(d_dk ** 2))
+    d_phi, d_dk = d_phi / norm, d_dk / norm
+    slope = float(np.dot(gphi, d_phi) + np.dot(gdk, d_dk * (1.0 / wl.MM)))
+    def cd(eps):
+        Jp = s.adjoint_forward(dev, dk + eps * d_dk / wl.MM, p.nz, p.dz, w, phi=phi + eps * d_phi)
+        Jm = s.adjoint_forward(dev, dk - eps * d_dk / wl.MM, p.nz, p.dz, w, phi=phi - eps * d_phi)
+        return (Jp - Jm) / (2 * eps)
+
+    # steps that move eta by ~0.8% and ~0.4%; Richardson removes the O(eps^2) term
+    eps = 0.008 * J / slope
+    f1, f2 = cd(eps), cd(0.5 * eps)
+    rich = (4 * f2 - f1) / 3
+    s.close()
+    assert abs(rich / slope - 1) < GRAD_TOL, (f1, f2, rich, slope)
+
+
+def test_autograd_function():
+    import paper_2609_08384_gb300 as br
+    nz, dz = 20, 20 * wl.UM
+    g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 70)
+    w = br.shg_efficiency_weights(f, ins[1].astype(np.complex128))
+    s = br.Solver(g, f, wl.D_EFF, 0.0)
+    dev = [torch.from_numpy(a).cuda() for a in ins]
+    Eta = br.shg_efficiency_function()
+    tphi = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
+    tdk = torch.tensor(dk, dtype=torch.float64, requires_grad=True)
+    eta = Eta.apply(tphi, tdk, s, dev, nz, dz, w, 0)
+    eta.backward()
+    J, gphi, gdk = _gpu_grad(g, f, ins, phi, dk, nz, dz, w)
+    assert float(eta.detach()) == J
+    assert np.array_equal(tphi.grad.numpy(), gphi) and np.array_equal(tdk.grad.numpy(), gdk)
+    # the incoming gradient scales the result (FP32 rounding of the scaled adjoint aside)
+    tphi.grad = None
+    tdk.grad = None
+    (3.0 * Eta.apply(tphi, tdk, s, dev, nz, dz, w, 0)).backward()
+    assert rel_l2(tphi.grad.numpy(), 3.0 * gphi) < 1e-4 and rel_l2(tdk.grad.numpy(), 3.0 * gdk) < 1e-4
+    s.close()
