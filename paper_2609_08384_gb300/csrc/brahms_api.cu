@@ -99,10 +99,9 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->partial = (double*)(ctx->ws + ctx->L.partial);
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
   cudaError_t e = cudaSuccess;
-  if (e == cudaSuccess) e = brahms::run_twiddles(ctx->twx, nx, ctx->stream);
-  if (e == cudaSuccess) e = brahms::run_twiddles(ctx->twy, ny, ctx->stream);
-  if (e == cudaSuccess) e = brahms::run_twiddles(ctx->twt, nt, ctx->stream);
-  ctx->launches += 3;
+  if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
+  if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
+  if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twt, nt, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     brahms_free(ctx);

@@ -49,8 +49,8 @@ struct ShapeT {
   static constexpr int TTPC = tiles_per_cta_t<PT, kBT>();
   static constexpr int smem_floats2() {
     const int x = xtile_smem_floats2<NXY, kBT>(2);
-    const int y = 2 * NXY + YTPC * NXY * col_tile_n(NXY);
-    const int t = 2 * NT + TTPC * NT * col_tile_n(NT);
+    const int y = 2 * tw_table_size<PY>() + YTPC * NXY * col_tile_n(NXY);
+    const int t = 2 * tw_table_size<PT>() + TTPC * NT * col_tile_n(NT);
     return x > y ? (x > t ? x : t) : (y > t ? y : t);
   }
 };
@@ -187,14 +187,12 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
       p.phiA = I.dk * ((it.step + 1) * I.dz);
       p.dkA = I.dk;
     }
-    float2* coef = reinterpret_cast<float2*>(tw + NXY);
-    float2* xch = coef + 12;
-    float2* stash = xch + xtile_rows<NXY, kBT>() * XchRow::pitch(NXY);
-    for (int i = threadIdx.x; i < NXY; i += kBT) tw[i] = I.twx[i];
+    float2* coef = reinterpret_cast<float2*>(sm4);
+    float2* rowbuf = coef + 12;
     nl_coefficients<2>(p, coef);
     __syncthreads();
     for (long long c = 0; c < it.ntiles; ++c) {
-      xpass_tile<NXY, 2, kBT>(p, it.tile + c, tw, coef, xch, stash);
+      xpass_tile<NXY, 2, kBT>(p, it.tile + c, coef, rowbuf);
       __syncthreads();
     }
     return;
@@ -214,23 +212,23 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
     a.xtiles = (NXY + col_tile_n(NT) - 1) / col_tile_n(NT);
     a.ntiles = 2LL * NXY * a.xtiles;
     a.tw = I.twt;
-    float2* xch = reinterpret_cast<float2*>(tw + NT);
-    for (int i = threadIdx.x; i < NT; i += kBT) tw[i] = I.twt[i];
+    float2* xch = reinterpret_cast<float2*>(tw + tw_table_size<typename SH::PT>());
+    for (int i = threadIdx.x; i < tw_table_size<typename SH::PT>(); i += kBT) tw[i] = I.twt[i];
     __syncthreads();
     for (long long c = 0; c < it.ntiles; ++c) {
-      tprop_tile<typename SH::PT, kBT>(a, it.tile + c, tw, xch);
+      tprop_tile<typename SH::PT, kBT>(a, it.tile + c, TwShared{tw}, xch);
       __syncthreads();
     }
   } else {
     a.xtiles = (NXY + col_tile_n(NXY) - 1) / col_tile_n(NXY);
     a.ntiles = 2LL * NT * a.xtiles;
     a.tw = I.twx;
-    float2* xch = reinterpret_cast<float2*>(tw + NXY);
-    for (int i = threadIdx.x; i < NXY; i += kBT) tw[i] = I.twx[i];
+    float2* xch = reinterpret_cast<float2*>(tw + tw_table_size<typename SH::PY>());
+    for (int i = threadIdx.x; i < tw_table_size<typename SH::PY>(); i += kBT) tw[i] = I.twx[i];
     __syncthreads();
     for (long long c = 0; c < it.ntiles; ++c) {
-      if (it.type == kTypeYF) axis_tile<typename SH::PY, false, 1, kBT>(a, it.tile + c, tw, xch);
-      else axis_tile<typename SH::PY, true, 1, kBT>(a, it.tile + c, tw, xch);
+      if (it.type == kTypeYF) axis_tile<typename SH::PY, false, 1, kBT>(a, it.tile + c, TwShared{tw}, xch);
+      else axis_tile<typename SH::PY, true, 1, kBT>(a, it.tile + c, TwShared{tw}, xch);
       __syncthreads();
     }
   }
@@ -529,9 +527,9 @@ brahms_status build_tables_for(brahms_batch* b, BatchInstHost& I) {
     a.alpha[f] = I.fp[f].alpha;
   }
   BB_CK(run_prop_tables(a, b->stream));
-  BB_CK(run_twiddles(I.twx, I.nx, b->stream));
-  BB_CK(run_twiddles(I.twt, I.nt, b->stream));
-  b->launches += 3;
+  BB_CK(upload_twiddles(I.twx, I.nx, b->stream));
+  BB_CK(upload_twiddles(I.twt, I.nt, b->stream));
+  b->launches += 1;
   return BRAHMS_OK;
 }
 
@@ -589,8 +587,9 @@ brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double d
   I.fp[0] = fp[0];
   I.fp[1] = fp[1];
   const size_t n = (size_t)I.npoints();
-  size_t o_state = 0, o_twx = al256(sizeof(float2) * 2 * n), o_twt = o_twx + al256(sizeof(float4) * nx),
-         o_px = o_twt + al256(sizeof(float4) * nt), o_py = o_px + al256(sizeof(float2) * 2 * nx),
+  size_t o_state = 0, o_twx = al256(sizeof(float2) * 2 * n),
+         o_twt = o_twx + al256(sizeof(float4) * tw_table_size_of(nx)),
+         o_px = o_twt + al256(sizeof(float4) * tw_table_size_of(nt)), o_py = o_px + al256(sizeof(float2) * 2 * nx),
          o_pt = o_py + al256(sizeof(float2) * 2 * ny), total = o_pt + al256(sizeof(float2) * 2 * nt);
   if (cudaMalloc((void**)&I.mem, total) != cudaSuccess) {
     cudaGetLastError();

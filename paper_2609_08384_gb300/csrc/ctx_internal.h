@@ -39,9 +39,9 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.px = take(sizeof(float2) * nx * nf);
   L.py = take(sizeof(float2) * ny * nf);
   L.pt = take(sizeof(float2) * nt * nf);
-  L.twx = take(sizeof(float4) * nx);
-  L.twy = take(sizeof(float4) * ny);
-  L.twt = take(sizeof(float4) * nt);
+  L.twx = take(sizeof(float4) * brahms::tw_table_size_of(nx));
+  L.twy = take(sizeof(float4) * brahms::tw_table_size_of(ny));
+  L.twt = take(sizeof(float4) * brahms::tw_table_size_of(nt));
   L.partial = take(sizeof(double) * kRedBlocks * nf);
   L.energy = take(sizeof(double) * nf);
   L.total = off;

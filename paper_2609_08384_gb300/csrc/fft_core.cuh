@@ -249,11 +249,50 @@ struct XchCol {
   __device__ __forceinline__ float2 ld(int pos) const { return base[pos * TX + tx]; }
 };
 
-// Twiddle tables hold W_N^k = (c, s) as hi + lo float pairs, float4 (ch, sh,
-// cl, sl): a product with the table is then correctly rounded, so the FFT
-// carries no systematic modulus error from rounded twiddles.
+// Twiddle tables hold W = (c, s) as hi + lo float pairs, float4 (ch, sh, cl,
+// sl): a product with the table is then correctly rounded, so the FFT carries
+// no systematic modulus error from rounded twiddles.
 __device__ __forceinline__ float2 tw_mul(float2 a, float4 w) { return twx<true>(a, w.x, w.z, w.y, w.w); }
-__device__ __forceinline__ float2 tw_mulc(float2 a, float4 w) { return twx<false>(a, w.x, w.z, w.y, w.w); }
+
+// Per-pass layout: pass P >= 1 of a direction with radix R and stride NS owns
+// the R x NS block [r][m] = exp(-/+ 2 pi i r m / (NS R)) (inverse entries are
+// stored conjugated), so the threads of a warp, whose butterflies have
+// consecutive m, read consecutive entries.  Forward blocks come first.
+template <class PL, bool INV>
+__host__ __device__ constexpr int tw_dir_size() {
+  int s = 0, ns = 1;
+  for (int q = 0; q < PL::NP; ++q) {
+    const int r = INV ? PL::r(PL::NP - 1 - q) : PL::r(q);
+    if (q > 0) s += r * ns;
+    ns *= r;
+  }
+  return s;
+}
+template <class PL, bool INV>
+__host__ __device__ constexpr int tw_pass_off(int P) {
+  int o = INV ? tw_dir_size<PL, false>() : 0, ns = 1;
+  for (int q = 0; q < P; ++q) {
+    const int r = INV ? PL::r(PL::NP - 1 - q) : PL::r(q);
+    if (q > 0) o += r * ns;
+    ns *= r;
+  }
+  return o;
+}
+template <class PL>
+__host__ __device__ constexpr int tw_table_size() {
+  return tw_dir_size<PL, false>() + tw_dir_size<PL, true>() > 0 ? tw_dir_size<PL, false>() + tw_dir_size<PL, true>()
+                                                                  : 1;
+}
+
+// twiddle access from shared memory or, read-only, through L1
+struct TwShared {
+  const float4* p;
+  __device__ __forceinline__ float4 operator()(int i) const { return p[i]; }
+};
+struct TwGlobal {
+  const float4* p;
+  __device__ __forceinline__ float4 operator()(int i) const { return __ldg(p + i); }
+};
 
 // Barrier used around shared-memory exchanges: the whole CTA, or only the
 // warp when every pencil's threads lie inside one warp.
@@ -266,8 +305,8 @@ struct SyncWarp {
 
 // Passes P..NP-1 of a length-N transform on the registers v (see header).
 // Every thread that shares a barrier of type S must call this.
-template <class PL, bool INV, int P, class X, class S = SyncBlock>
-__device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, const float4* __restrict__ tw) {
+template <class PL, bool INV, int P, class X, class S = SyncBlock, class TW = TwShared>
+__device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, const TW& tw) {
   constexpr int N = PL::N;
   constexpr int NP = PL::NP;
   constexpr int E = PL::E;
@@ -283,8 +322,7 @@ __device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, c
       const int m = j % NS;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        const float4 w = tw[r * m * (N / (NS * R))];
-        v[b * R + r] = INV ? tw_mulc(v[b * R + r], w) : tw_mul(v[b * R + r], w);
+        v[b * R + r] = tw_mul(v[b * R + r], tw(tw_pass_off<PL, INV>(P) + r * NS + m));
       }
     }
   }
@@ -309,7 +347,7 @@ __device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, c
 #pragma unroll
       for (int r = 0; r < R2; ++r) v[b * R2 + r] = x.ld(j + r * (N / R2));
     }
-    fft_run<PL, INV, P + 1, X, S>(v, t, x, tw);
+    fft_run<PL, INV, P + 1, X, S, TW>(v, t, x, tw);
   }
 }
 

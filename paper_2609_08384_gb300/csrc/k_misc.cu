@@ -3,22 +3,6 @@
 
 namespace brahms {
 
-// tw[k] = exp(-2 pi i k / n) evaluated in FP64 and split into hi + lo floats.
-__global__ void twiddle_kernel(float4* tw, int n) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) {
-    double s, c;
-    sincospi(-2.0 * (double)k / (double)n, &s, &c);
-    const float ch = (float)c, sh = (float)s;
-    tw[k] = make_float4(ch, sh, (float)(c - (double)ch), (float)(s - (double)sh));
-  }
-}
-
-cudaError_t run_twiddles(float4* tw, int n, cudaStream_t s) {
-  twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
-  return cudaPeekAtLastError();
-}
-
 // 2 pi * numpy.fft.fftfreq(n, d)[m]; the Nyquist bin is negative.
 __device__ __forceinline__ double ang_freq(int m, int n, double d) {
   const int mm = (m < (n + 1) / 2) ? m : m - n;

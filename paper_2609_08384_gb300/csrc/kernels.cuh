@@ -28,7 +28,7 @@ struct XPassArgs {
   float2* data;        // [nf][rows][nx]
   long long fstride;   // elements between fields
   long long rows;      // ny * nt
-  const float4* tw;    // e^{-2 pi i k / nx}, k < nx, as hi/lo pairs
+  const float4* tw;    // per-pass twiddle table of the x transform (hi/lo pairs)
   int mode;            // XMode
   double phiA, dkA;    // step whose first half is applied: Phi(z_j), dk_j
   double phiB, dkB;    // step whose second half is applied
@@ -67,8 +67,8 @@ __host__ __device__ constexpr bool xpass_warp_sync() { return fft_threads<N>() <
 // exchange rows, and a private stash of F-1 fields per thread
 template <int N>
 __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
-  return 2 * N + 6 * nf + xpass_rows<N>() * XchRow::pitch(N) + (nf - 1) * FftPlan<N>::E * xpass_threads<N>();
-}  // equals xtile_smem_floats2<N, xpass_threads<N>()>(nf)
+  return 6 * nf + nf * xpass_rows<N>() * XchRow::pitch(N);
+}
 
 // Strided pencils: tiles of TX neighbouring columns (128-byte rows up to
 // N = 1024) times the plan's T threads per pencil.
@@ -77,9 +77,12 @@ template <class PL>
 __host__ __device__ constexpr int tile_threads() { return PL::T * col_tile_n(PL::N); }
 template <class PL>
 __host__ __device__ constexpr int tiles_per_cta() { return tile_threads<PL>() >= 256 ? 1 : 256 / tile_threads<PL>(); }
+// twiddle tables up to 40 KB are copied to shared memory; larger ones are read through L1
+template <class PL>
+__host__ __device__ constexpr bool tw_in_smem() { return tw_table_size<PL>() * 16 <= 40960; }
 template <class PL>
 __host__ __device__ constexpr int axis_smem_floats2() {
-  return 2 * PL::N + tiles_per_cta<PL>() * PL::N * col_tile_n(PL::N);
+  return (tw_in_smem<PL>() ? 2 * tw_table_size<PL>() : 0) + tiles_per_cta<PL>() * PL::N * col_tile_n(PL::N);
 }
 
 // -------------------------------------------------------- nonlinear step
@@ -161,21 +164,26 @@ __device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef
 
 // ------------------------------------------------------------------ x-pass
 // One row (y, tau) of every field per T threads; a CTA of THREADS threads
-// handles THREADS/T rows per tile.  Fields 0..F-2 are parked in a per-thread
-// shared-memory stash after their inverse transform, so only one field's E
-// values occupy registers at a time; the pointwise RK4 pair reads all F
-// values of a point from the stash and the registers.  Field data is read
-// with ld.global.cg (L2), so a tile may follow a pass written by other SMs.
+// handles THREADS/T rows per tile.  Each field of a row has its own padded
+// row buffer in shared memory, used both as that field's FFT exchange space
+// and to park the field between the transforms: after the inverse transform
+// every thread parks its values at the positions it owns (the last pass of a
+// Stockham transform reads and writes the same positions per thread), the
+// pointwise RK4 pair then reads all F values of each owned point, and the
+// forward transform starts from the owned positions again.  No thread ever
+// reads a position another thread parked, so parking needs no barrier, and
+// the fields and the points are processed in loops rather than unrolled,
+// which keeps the kernel small enough for the instruction cache.  Field data
+// is read with ld.global.cg (L2), twiddles through L1.
 template <int NX, int THREADS>
 __host__ __device__ constexpr int xtile_rows() { return THREADS / FftPlan<NX>::T; }
 template <int NX, int THREADS>
 __host__ __device__ constexpr int xtile_smem_floats2(int nf) {
-  return 2 * NX + 6 * nf + xtile_rows<NX, THREADS>() * XchRow::pitch(NX) + (nf - 1) * FftPlan<NX>::E * THREADS;
+  return 6 * nf + nf * xtile_rows<NX, THREADS>() * XchRow::pitch(NX);
 }
 
 template <int NX, int F, int THREADS>
-__device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, const float4* tw,
-                                           const float2* coef, float2* xch, float2* stash_all) {
+__device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, const float2* coef, float2* rowbuf) {
   using PL = FftPlan<NX>;
   constexpr int E = PL::E;
   constexpr int T = PL::T;
@@ -186,30 +194,30 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
   constexpr int SF0 = NX / RF0, SFL = NX / RFL;
   using SY = typename std::conditional<xpass_warp_sync<NX>(), SyncWarp, SyncBlock>::type;
   static_assert(ROWS >= 1 && ROWS * T == THREADS, "CTA must hold whole rows");
-  float2* stash = stash_all + threadIdx.x;  // stash[(f E + e) THREADS]
+  const TwGlobal tw{p.tw};
 
   const int t = threadIdx.x % T;
   const int rl = threadIdx.x / T;
   const long long row = tile * ROWS + rl;
   const bool act = row < p.rows;
-  const XchRow xr{xch + rl * PITCH};
+  float2* myrow = rowbuf + rl * PITCH;  // field f at myrow + f ROWS PITCH
   const int mode = p.mode;
   const bool from_k = (mode == XM_INV || mode == XM_NL_MID || mode == XM_NL_LAST);
 
-  float2 v[E];
-  // The inverse transform's first pass reads positions t + b T + r NX/RFL and
-  // ends at t + b T + r NX/RF0, which are the forward transform's first-pass
-  // positions: values flow from one to the other without an exchange.
-#pragma unroll
+  // 1. every field: load, inverse transform (from k-space), park
+#pragma unroll 1
   for (int f = 0; f < F; ++f) {
+    const XchRow xr{myrow + f * ROWS * PITCH};
     const float2* src = p.data + f * p.fstride + (act ? row : 0) * NX;
+    float2 v[E];
     if (from_k) {
 #pragma unroll
       for (int b = 0; b < E / RFL; ++b)
 #pragma unroll
         for (int r = 0; r < RFL; ++r)
           v[b * RFL + r] = act ? __ldcg(src + t + b * T + r * SFL) : make_float2(0.f, 0.f);
-      fft_run<PL, true, 0, XchRow, SY>(v, t, xr, tw);
+      // inverse's output positions t + b T + r NX/RF0 = forward first-pass positions
+      fft_run<PL, true, 0, XchRow, SY, TwGlobal>(v, t, xr, tw);
     } else {
 #pragma unroll
       for (int b = 0; b < E / RF0; ++b)
@@ -217,37 +225,40 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
         for (int r = 0; r < RF0; ++r)
           v[b * RF0 + r] = act ? __ldcg(src + t + b * T + r * SF0) : make_float2(0.f, 0.f);
     }
-    if (f < F - 1) {
 #pragma unroll
-      for (int e = 0; e < E; ++e) stash[(f * E + e) * THREADS] = v[e];
-    }
+    for (int b = 0; b < E / RF0; ++b)
+#pragma unroll
+      for (int r = 0; r < RF0; ++r) xr.st(t + b * T + r * SF0, v[b * RF0 + r]);
   }
 
+  // 2. the RK4 half steps, point by point over the owned positions
   if (mode == XM_NL_MID || mode == XM_NL_LAST || mode == XM_NL_FIRST) {
-#pragma unroll
+#pragma unroll 1
     for (int e = 0; e < E; ++e) {
+      const int pos = t + (e / RF0) * T + (e % RF0) * SF0;
+      const int off = pos + (pos >> 4);  // XchRow padding
       float2 a[F];
 #pragma unroll
-      for (int f = 0; f < F - 1; ++f) a[f] = stash[(f * E + e) * THREADS];
-      a[F - 1] = v[e];
+      for (int f = 0; f < F; ++f) a[f] = myrow[f * ROWS * PITCH + off];
       if (mode != XM_NL_FIRST) rk4<F>(a, coef);
       if (mode != XM_NL_LAST) rk4<F>(a, coef + 3 * F);
 #pragma unroll
-      for (int f = 0; f < F - 1; ++f) stash[(f * E + e) * THREADS] = a[f];
-      v[e] = a[F - 1];
+      for (int f = 0; f < F; ++f) myrow[f * ROWS * PITCH + off] = a[f];
     }
   }
 
+  // 3. every field: unpark, forward transform (or scale), store
   const bool to_x = (mode == XM_INV || mode == XM_NL_LAST);
   const float sc = mode == XM_INV ? p.scale : 1.f;
-#pragma unroll
-  for (int g = 0; g < F; ++g) {
-    const int f = (g + F - 1) % F;  // the field in registers first, then the stash
-    if (f < F - 1) {
-#pragma unroll
-      for (int e = 0; e < E; ++e) v[e] = stash[(f * E + e) * THREADS];
-    }
+#pragma unroll 1
+  for (int f = 0; f < F; ++f) {
+    const XchRow xr{myrow + f * ROWS * PITCH};
     float2* dst = p.data + f * p.fstride + (act ? row : 0) * NX;
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < E / RF0; ++b)
+#pragma unroll
+      for (int r = 0; r < RF0; ++r) v[b * RF0 + r] = xr.ld(t + b * T + r * SF0);
     if (to_x) {
       if (act) {
 #pragma unroll
@@ -256,7 +267,7 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
           for (int r = 0; r < RF0; ++r) dst[t + b * T + r * SF0] = cscale(v[b * RF0 + r], sc);
       }
     } else {
-      fft_run<PL, false, 0, XchRow, SY>(v, t, xr, tw);
+      fft_run<PL, false, 0, XchRow, SY, TwGlobal>(v, t, xr, tw);
       if (act) {
 #pragma unroll
         for (int b = 0; b < E / RFL; ++b)
@@ -264,6 +275,7 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
           for (int r = 0; r < RFL; ++r) dst[t + b * T + r * SFL] = v[b * RFL + r];
       }
     }
+    SY::sync();  // the next field's exchanges use another buffer; keep the warp together
   }
 }
 
@@ -272,14 +284,11 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
     xpass_kernel(const XPassArgs p) {
   constexpr int THREADS = xpass_threads<NX>();
   extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* coef = reinterpret_cast<float2*>(tw + NX);
-  float2* xch = coef + 6 * F;
-  float2* stash = xch + xtile_rows<NX, THREADS>() * XchRow::pitch(NX);
-  for (int i = threadIdx.x; i < NX; i += blockDim.x) tw[i] = p.tw[i];
+  float2* coef = reinterpret_cast<float2*>(sm4);
+  float2* rowbuf = coef + 6 * F;
   nl_coefficients<F>(p, coef);
   __syncthreads();
-  xpass_tile<NX, F, THREADS>(p, blockIdx.x, tw, coef, xch, stash);
+  xpass_tile<NX, F, THREADS>(p, blockIdx.x, coef, rowbuf);
 }
 
 // ------------------------------------------------- strided-axis passes
@@ -310,8 +319,8 @@ struct AxisTile {
 template <class PL, int THREADS>
 __host__ __device__ constexpr int tiles_per_cta_t() { return THREADS / tile_threads<PL>(); }
 
-template <class PL, bool INV, int AXIS, int THREADS>
-__device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile, const float4* tw, float2* xch) {
+template <class PL, bool INV, int AXIS, int THREADS, class TW = TwShared>
+__device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile, const TW& tw, float2* xch) {
   constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
   constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
   static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
@@ -327,7 +336,7 @@ __device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile,
 #pragma unroll
     for (int r = 0; r < R0; ++r)
       v[b * R0 + r] = a.act ? __ldcg(a.base + (t + b * T + r * S0) * a.stride) : make_float2(0.f, 0.f);
-  fft_run<PL, INV, 0>(v, t, xc, tw);
+  fft_run<PL, INV, 0, XchCol<TX>, SyncBlock, TW>(v, t, xc, tw);
   if (a.act) {
 #pragma unroll
     for (int b = 0; b < E / RL; ++b)
@@ -337,8 +346,8 @@ __device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile,
 }
 
 // Forward tau-FFT, propagator multiply, inverse tau-FFT, in one pass.
-template <class PL, int THREADS>
-__device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile, const float4* tw, float2* xch) {
+template <class PL, int THREADS, class TW = TwShared>
+__device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile, const TW& tw, float2* xch) {
   constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
   constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
   static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
@@ -354,7 +363,7 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
 #pragma unroll
     for (int r = 0; r < R0; ++r)
       v[b * R0 + r] = a.act ? __ldcg(a.base + (t + b * T + r * S0) * a.stride) : make_float2(0.f, 0.f);
-  fft_run<PL, false, 0>(v, t, xc, tw);
+  fft_run<PL, false, 0, XchCol<TX>, SyncBlock, TW>(v, t, xc, tw);
   // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL.
   // P = (1 + Dx)(1 + Dy)(1 + Dt) applied as w + w D with w = v/(nx ny nt).
   float2 dxy = make_float2(0.f, 0.f);
@@ -378,7 +387,7 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
       v[b * RL + r] = cadd(w, cmul(w, d));
     }
   // the inverse's first pass reads exactly these positions
-  fft_run<PL, true, 0>(v, t, xc, tw);
+  fft_run<PL, true, 0, XchCol<TX>, SyncBlock, TW>(v, t, xc, tw);
   if (a.act) {
 #pragma unroll
     for (int b = 0; b < E / R0; ++b)
@@ -392,11 +401,15 @@ __global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
     axis_fft_kernel(const AxisArgs p) {
   constexpr int THREADS = tiles_per_cta<PL>() * tile_threads<PL>();
   extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* xch = reinterpret_cast<float2*>(tw + PL::N);
-  for (int i = threadIdx.x; i < PL::N; i += blockDim.x) tw[i] = p.tw[i];
-  __syncthreads();
-  axis_tile<PL, INV, AXIS, THREADS>(p, blockIdx.x, tw, xch);
+  if constexpr (tw_in_smem<PL>()) {
+    float4* tw = sm4;
+    for (int i = threadIdx.x; i < tw_table_size<PL>(); i += blockDim.x) tw[i] = p.tw[i];
+    __syncthreads();
+    axis_tile<PL, INV, AXIS, THREADS>(p, blockIdx.x, TwShared{tw},
+                                      reinterpret_cast<float2*>(tw + tw_table_size<PL>()));
+  } else {
+    axis_tile<PL, INV, AXIS, THREADS>(p, blockIdx.x, TwGlobal{p.tw}, reinterpret_cast<float2*>(sm4));
+  }
 }
 
 template <class PL>
@@ -404,11 +417,14 @@ __global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
     tpass_prop_kernel(const AxisArgs p) {
   constexpr int THREADS = tiles_per_cta<PL>() * tile_threads<PL>();
   extern __shared__ float4 sm4[];
-  float4* tw = sm4;
-  float2* xch = reinterpret_cast<float2*>(tw + PL::N);
-  for (int i = threadIdx.x; i < PL::N; i += blockDim.x) tw[i] = p.tw[i];
-  __syncthreads();
-  tprop_tile<PL, THREADS>(p, blockIdx.x, tw, xch);
+  if constexpr (tw_in_smem<PL>()) {
+    float4* tw = sm4;
+    for (int i = threadIdx.x; i < tw_table_size<PL>(); i += blockDim.x) tw[i] = p.tw[i];
+    __syncthreads();
+    tprop_tile<PL, THREADS>(p, blockIdx.x, TwShared{tw}, reinterpret_cast<float2*>(tw + tw_table_size<PL>()));
+  } else {
+    tprop_tile<PL, THREADS>(p, blockIdx.x, TwGlobal{p.tw}, reinterpret_cast<float2*>(sm4));
+  }
 }
 
 // ------------------------------------------------------------ dispatchers
@@ -420,7 +436,10 @@ bool size_supported(int n);
 int col_tile_of(int n);
 
 // misc kernels (k_misc.cu)
-cudaError_t run_twiddles(float4* tw, int n, cudaStream_t s);
+// per-pass twiddle table of the default plan of length n (host-built, FP64
+// split into hi + lo floats), and its size in float4 entries
+int tw_table_size_of(int n);
+cudaError_t upload_twiddles(float4* tw, int n, cudaStream_t s);
 struct TableArgs {
   float2* px;
   float2* py;
