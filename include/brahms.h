@@ -123,6 +123,16 @@ brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
  * 4 other) are written to the first nkinds entries; this waits for the stream. */
 brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* launches, int nkinds);
 
+/* Implementation options.  BRAHMS_OPT_TMA_TAU: value 16 or 8 makes the
+ * tau-pass of brahms_propagate a persistent kernel that stages tiles of that
+ * many x columns through shared memory with double-buffered TMA copies
+ * (needs nt in {256, 512} and nx >= 16, else E_SIZE); 0 (the default) keeps
+ * the plain tau-pass.  Both compute identical numbers.  E_ARG for an unknown
+ * option or value.  brahms_get_option returns the current value or -1. */
+enum { BRAHMS_OPT_TMA_TAU = 1 };
+brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value);
+int brahms_get_option(const brahms_ctx* ctx, int option);
+
 /* Number of kernel launches this context has enqueued since creation. */
 long long brahms_launch_count(const brahms_ctx* ctx);
 

@@ -30,6 +30,7 @@ BRAHMS_C64 = 0
 BRAHMS_C128 = 1
 
 KIND_NAMES = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
+BRAHMS_OPT_TMA_TAU = 1
 
 # Every entry point declared in include/brahms.h, with its ctypes signature.
 _c = ctypes
@@ -58,6 +59,8 @@ SIGNATURES = {
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
     "brahms_launch_count": (_c.c_longlong, [_vp]),
+    "brahms_set_option": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
+    "brahms_get_option": (_c.c_int, [_vp, _c.c_int]),
     "brahms_energy_static": (_c.c_int, [_c.POINTER(_vp), _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_double,
                                         _c.c_double, _c.c_double, _c.POINTER(FieldParams), _vp, _vp]),
     "brahms_adjoint_forward": (_c.c_int, [_vp, _c.POINTER(_vp), _c.c_int, _c.c_int, _dp, _c.c_int, _dp, _c.c_int,
@@ -233,6 +236,12 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(load().brahms_launch_count(self.ctx))
+
+    def set_option(self, option: int, value: int):
+        _check(self.ctx, load().brahms_set_option(self.ctx, int(option), int(value)))
+
+    def get_option(self, option: int) -> int:
+        return int(load().brahms_get_option(self.ctx, int(option)))
 
     def adjoint_forward(self, fields, dk, nz, dz, weights, phi=None, phi_field=1, checkpoint_interval=0):
         """J = sum_f w_f sum |A_f(L)|^2 after the phase phi (centred order) and

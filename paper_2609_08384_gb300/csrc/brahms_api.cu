@@ -84,7 +84,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
     ctx->ws = (char*)p;
     ctx->own_ws = true;
   }
-  if (cudaMallocHost((void**)&ctx->energy_host, sizeof(double) * 3) != cudaSuccess) {
+  if (cudaMallocHost((void**)&ctx->energy_host, sizeof(double) * 4) != cudaSuccess) {
     cudaGetLastError();
     brahms_free(ctx);
     return BRAHMS_E_OOM;
@@ -98,10 +98,12 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->twt = (float4*)(ctx->ws + ctx->L.twt);
   ctx->partial = (double*)(ctx->ws + ctx->L.partial);
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
+  ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twt, nt, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     brahms_free(ctx);
@@ -190,7 +192,12 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   for (int i = 0; i < nz; ++i, ++j) {
     const double dkj = dk_of_step(ctx, j);
     BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
-    BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
+    if (ctx->use_tma)
+      BR_CK(launch(ctx, 2, 1, [&] {
+        return brahms::run_tpass_prop_tma(nt, ctx->use_tma, ctx->tmap_state, at, ctx->dev_err, ctx->stream);
+      }));
+    else
+      BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
     BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ay, ctx->stream); }));
     const bool last = (i == nz - 1);
     brahms::XPassArgs a = xargs(ctx, last ? brahms::XM_NL_LAST : brahms::XM_NL_MID, dz);
@@ -301,5 +308,28 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
 }
 
 long long brahms_launch_count(const brahms_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (option == BRAHMS_OPT_TMA_TAU) {
+    if (!value) {
+      ctx->use_tma = 0;
+      return BRAHMS_OK;
+    }
+    if (value != 8 && value != 16) return fail(ctx, BRAHMS_E_ARG, "TMA tile width must be 8 or 16 columns");
+    if (!brahms::tma_tau_supported(ctx->nx, ctx->nt))
+      return fail(ctx, BRAHMS_E_SIZE, "TMA tau-pass needs nt in {256, 512} and nx >= 16");
+    BR_CK(brahms::make_tau_tensor_map(ctx->tmap_state, ctx->state, ctx->nx, ctx->ny, ctx->nt, ctx->nf, value));
+    ctx->use_tma = value;
+    return BRAHMS_OK;
+  }
+  return fail(ctx, BRAHMS_E_ARG, "unknown option");
+}
+
+int brahms_get_option(const brahms_ctx* ctx, int option) {
+  if (!ctx) return -1;
+  if (option == BRAHMS_OPT_TMA_TAU) return ctx->use_tma;
+  return -1;
+}
 
 }  // extern "C"

@@ -23,7 +23,7 @@ constexpr int kKinds = 5;
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t state, px, py, pt, twx, twy, twt, partial, energy, total;
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, total;
 };
 
 inline Layout make_layout(int nx, int ny, int nt, int nf) {
@@ -44,6 +44,7 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.twt = take(sizeof(float4) * brahms::tw_table_size_of(nt));
   L.partial = take(sizeof(double) * kRedBlocks * nf);
   L.energy = take(sizeof(double) * nf);
+  L.err = take(sizeof(int));
   L.total = off;
   return L;
 }
@@ -68,7 +69,10 @@ struct brahms_ctx {
   float2 *state = nullptr, *px = nullptr, *py = nullptr, *pt = nullptr;
   float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
   double *partial = nullptr, *energy_dev = nullptr;
-  double* energy_host = nullptr;  // pinned, nf entries
+  double* energy_host = nullptr;  // pinned, nf entries + the device error word
+  int* dev_err = nullptr;          // set by kernels whose bounded waits expired
+  alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
+  int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns
   double tab_dz = NAN;
   bool have_fields = false;
   double z = 0.0, phi = 0.0;
@@ -258,7 +262,13 @@ inline brahms_status enqueue_energy(brahms_ctx* ctx) {
 inline brahms_status finish_with_check(brahms_ctx* ctx) {
   brahms_status s = enqueue_energy(ctx);
   if (s != BRAHMS_OK) return s;
+  int* herr = reinterpret_cast<int*>(ctx->energy_host + 3);
+  BR_CK(cudaMemcpyAsync(herr, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   BR_CK(cudaStreamSynchronize(ctx->stream));
+  if (*herr != 0) {
+    BR_CK(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+    return fail(ctx, BRAHMS_E_TIMEOUT, "a bounded device wait expired (TMA copy not completed)");
+  }
   for (int f = 0; f < ctx->nf; ++f)
     if (!std::isfinite(ctx->energy_host[f]))
       return fail(ctx, BRAHMS_E_NONFINITE, "fields are not finite (dz too large for the coupling, Sec. 3.2)");

@@ -436,6 +436,11 @@ bool size_supported(int n);
 int col_tile_of(int n);
 
 // misc kernels (k_misc.cu)
+// TMA tau-pass (k_tma.cu)
+bool tma_tau_supported(int nx, int nt);
+cudaError_t make_tau_tensor_map(void* map128, const float2* data, int nx, int ny, int nt, int nf, int tx);
+cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err, cudaStream_t s);
+
 // per-pass twiddle table of the default plan of length n (host-built, FP64
 // split into hi + lo floats), and its size in float4 entries
 int tw_table_size_of(int n);

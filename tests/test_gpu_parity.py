@@ -313,3 +313,23 @@ def test_host_and_c128_paths_match_device_c64():
     for o in outs[1:]:
         for f in range(2):
             assert np.array_equal(np.asarray(o[f]).astype(np.complex64), outs[0][f])
+
+
+@pytest.mark.parametrize("maker", ["opg", "sfg"])
+def test_tma_tau_pass_is_bit_identical_to_plain(maker):
+    """The TMA-staged persistent tau-pass computes exactly what the plain
+    tau-pass computes (same arithmetic, different data movement)."""
+    br = _br()
+    p = wl.problem_opg() if maker == "opg" else wl.problem_sfg()
+    init = _dev(wl.inputs_opg(p) if maker == "opg" else wl.inputs_sfg(p))
+    outs = []
+    for tma in (16, 8, 0):
+        s = br.Solver(p.grid, p.fields, p.d_eff, p.dk)
+        s.set_option(br.BRAHMS_OPT_TMA_TAU, tma)
+        assert s.get_option(br.BRAHMS_OPT_TMA_TAU) == tma
+        s.set_fields(init)
+        s.propagate(5, p.dz)
+        outs.append(s.get_fields())
+        s.close()
+    for f in range(3):
+        assert np.array_equal(outs[0][f], outs[2][f]) and np.array_equal(outs[1][f], outs[2][f])
