@@ -233,7 +233,7 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
     float2* aw = ctx->adj_work + n;
     BR_CK(cudaMemcpyAsync(gw, ctx->adj_g + (size_t)pf * n, sizeof(float2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
     BR_CK(cudaMemcpyAsync(aw, ctx->adj_ckpt + (size_t)pf * n, sizeof(float2) * n, cudaMemcpyDeviceToDevice, ctx->stream));
-    brahms::AxisArgs at = aargs(ctx, 2);
+    brahms::AxisArgs at = aargs(ctx, 2, false);
     at.data = ctx->adj_work;
     at.ntiles = 2LL * ctx->ny * at.xtiles;  // the two copies
     BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, false, at, ctx->stream); }));

@@ -271,7 +271,7 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   if (!ctx) return BRAHMS_E_ARG;
   if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "no fields set");
   if (direction != -1 && direction != 1) return fail(ctx, BRAHMS_E_ARG, "direction must be -1 or +1");
-  const brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
+  const brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2, false);
   const bool inv = direction == 1;
   brahms::XPassArgs a = xargs(ctx, inv ? brahms::XM_INV : brahms::XM_FWD, 1.0);
   a.scale = (float)(1.0 / (double)ctx->npoints());

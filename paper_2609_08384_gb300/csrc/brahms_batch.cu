@@ -49,8 +49,8 @@ struct ShapeT {
   static constexpr int TTPC = tiles_per_cta_t<PT, kBT>();
   static constexpr int smem_floats2() {
     const int x = xtile_smem_floats2<NXY, kBT>(2);
-    const int y = 2 * tw_table_size<PY>() + YTPC * NXY * col_tile_n(NXY);
-    const int t = 2 * tw_table_size<PT>() + TTPC * NT * col_tile_n(NT);
+    const int y = 2 * tw_table_size<PY>() + YTPC * NXY * ColTile<PY>::value;
+    const int t = 2 * tw_table_size<PT>() + TTPC * NT * ColTile<PT>::value;
     return x > y ? (x > t ? x : t) : (y > t ? y : t);
   }
 };
@@ -209,7 +209,7 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
   a.scale = I.scale;
   a.scale_lo = I.scale_lo;
   if (it.type == kTypeT) {
-    a.xtiles = (NXY + col_tile_n(NT) - 1) / col_tile_n(NT);
+    a.xtiles = (NXY + ColTile<typename SH::PT>::value - 1) / ColTile<typename SH::PT>::value;
     a.ntiles = 2LL * NXY * a.xtiles;
     a.tw = I.twt;
     float2* xch = reinterpret_cast<float2*>(tw + tw_table_size<typename SH::PT>());
@@ -220,7 +220,7 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
       __syncthreads();
     }
   } else {
-    a.xtiles = (NXY + col_tile_n(NXY) - 1) / col_tile_n(NXY);
+    a.xtiles = (NXY + ColTile<typename SH::PY>::value - 1) / ColTile<typename SH::PY>::value;
     a.ntiles = 2LL * NT * a.xtiles;
     a.tw = I.twx;
     float2* xch = reinterpret_cast<float2*>(tw + tw_table_size<typename SH::PY>());
@@ -439,8 +439,8 @@ brahms_status prepare(brahms_batch* b) {
     d.scale_lo = (float)(inv_n - (double)d.scale);
     const int rows = xtile_rows_of(I.shape);
     d.ct_x = ((long long)I.ny * I.nt + rows - 1) / rows;
-    const long long ytiles = 2LL * I.nt * ((I.nx + col_tile_n(I.ny) - 1) / col_tile_n(I.ny));
-    const long long ttiles = 2LL * I.ny * ((I.nx + col_tile_n(I.nt) - 1) / col_tile_n(I.nt));
+    const long long ytiles = 2LL * I.nt * ((I.nx + col_tile_of(I.ny) - 1) / col_tile_of(I.ny));
+    const long long ttiles = 2LL * I.ny * ((I.nx + tau_col_tile_of(I.nt) - 1) / tau_col_tile_of(I.nt));
     d.ct_y = (ytiles + ytpc_of(I.shape) - 1) / ytpc_of(I.shape);
     d.ct_t = (ttiles + ttpc_of(I.shape) - 1) / ttpc_of(I.shape);
     d.g_x = b->gran[I.shape][0];

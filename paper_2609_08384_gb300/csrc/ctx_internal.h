@@ -223,7 +223,8 @@ inline brahms::XPassArgs xargs(brahms_ctx* c, int mode, double dz) {
   return a;
 }
 
-inline brahms::AxisArgs aargs(brahms_ctx* c, int axis) {
+// axis 1: y-pass; axis 2 with tau_prop: tau propagator; axis 2 without: tau FFT only
+inline brahms::AxisArgs aargs(brahms_ctx* c, int axis, bool tau_prop = true) {
   brahms::AxisArgs a{};
   a.data = c->state;
   a.nx = c->nx;
@@ -231,7 +232,7 @@ inline brahms::AxisArgs aargs(brahms_ctx* c, int axis) {
   a.nt = c->nt;
   a.fstride = c->npoints();
   const int n = axis == 1 ? c->ny : c->nt;
-  const int tx = brahms::col_tile_of(n);
+  const int tx = (axis == 2 && tau_prop) ? brahms::tau_col_tile_of(n) : brahms::col_tile_of(n);
   a.xtiles = (c->nx + tx - 1) / tx;
   a.ntiles = (long long)c->nf * (axis == 1 ? c->nt : c->ny) * a.xtiles;
   a.tw = axis == 1 ? c->twy : c->twt;

@@ -128,11 +128,23 @@ cudaError_t upload_twiddles(float4* tw, int n, cudaStream_t s) {
   return cudaStreamSynchronize(s);  // h is a local buffer
 }
 
+int tau_col_tile_of(int n) {
+  switch (n) {
+#define BRAHMS_TC_CASE(N) \
+  case N:                 \
+    return ColTile<TauPlan<N>>::value;
+    BRAHMS_FOR_EACH_SIZE(BRAHMS_TC_CASE)
+#undef BRAHMS_TC_CASE
+    default:
+      return 0;
+  }
+}
+
 int col_tile_of(int n) {
   switch (n) {
 #define BRAHMS_C_CASE(N) \
   case N:                \
-    return col_tile_n(N);
+    return ColTile<FftPlan<N>>::value;
     BRAHMS_FOR_EACH_SIZE(BRAHMS_C_CASE)
 #undef BRAHMS_C_CASE
     default:

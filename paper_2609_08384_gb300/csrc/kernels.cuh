@@ -73,8 +73,15 @@ __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
 // Strided pencils: tiles of TX neighbouring columns (128-byte rows up to
 // N = 1024) times the plan's T threads per pencil.
 __host__ __device__ constexpr int col_tile_n(int n) { return n <= 1024 ? 16 : (n <= 2048 ? 8 : 4); }
+// columns per tile of a plan's strided-pencil kernels
 template <class PL>
-__host__ __device__ constexpr int tile_threads() { return PL::T * col_tile_n(PL::N); }
+struct ColTile {
+  static constexpr int value = col_tile_n(PL::N);
+};
+// (A plan may override its tile width; 8-column tiles for the 512-point tau
+// propagator measured slower than 16 on GB300, 575 vs 546 us per OPG launch.)
+template <class PL>
+__host__ __device__ constexpr int tile_threads() { return PL::T * ColTile<PL>::value; }
 template <class PL>
 __host__ __device__ constexpr int tiles_per_cta() { return tile_threads<PL>() >= 256 ? 1 : 256 / tile_threads<PL>(); }
 // twiddle tables up to 40 KB are copied to shared memory; larger ones are read through L1
@@ -82,7 +89,7 @@ template <class PL>
 __host__ __device__ constexpr bool tw_in_smem() { return tw_table_size<PL>() * 16 <= 40960; }
 template <class PL>
 __host__ __device__ constexpr int axis_smem_floats2() {
-  return (tw_in_smem<PL>() ? 2 * tw_table_size<PL>() : 0) + tiles_per_cta<PL>() * PL::N * col_tile_n(PL::N);
+  return (tw_in_smem<PL>() ? 2 * tw_table_size<PL>() : 0) + tiles_per_cta<PL>() * PL::N * ColTile<PL>::value;
 }
 
 // -------------------------------------------------------- nonlinear step
@@ -294,14 +301,13 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
 // ------------------------------------------------- strided-axis passes
 // AXIS 1: pencils along y (stride nx), tiles over (f, tau, x-tile).
 // AXIS 2: pencils along tau (stride nx ny), tiles over (f, y, x-tile).
-template <int N, int AXIS>
+template <int N, int AXIS, int TX>
 struct AxisTile {
   float2* base;  // element (x, pencil index 0)
   long long stride;
   int f, other, x;
   bool act;
   __device__ __forceinline__ AxisTile(const AxisArgs& p, long long tile, int tx) {
-    constexpr int TX = col_tile_n(N);
     const int xt = (int)(tile % p.xtiles);
     const long long rest = tile / p.xtiles;
     const int no = AXIS == 1 ? p.nt : p.ny;
@@ -321,14 +327,14 @@ __host__ __device__ constexpr int tiles_per_cta_t() { return THREADS / tile_thre
 
 template <class PL, bool INV, int AXIS, int THREADS, class TW = TwShared>
 __device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile, const TW& tw, float2* xch) {
-  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
+  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = ColTile<PL>::value;
   constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
   static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
   constexpr int R0 = fft_radix<PL, INV>(0), RL = fft_radix<PL, INV>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
   const int tx = lt % TX, t = lt / TX;
-  const AxisTile<N, AXIS> a(p, cta_tile * TPC + tl, tx);
+  const AxisTile<N, AXIS, TX> a(p, cta_tile * TPC + tl, tx);
   const XchCol<TX> xc{xch + tl * N * TX, tx};
   float2 v[E];
 #pragma unroll
@@ -348,14 +354,14 @@ __device__ __forceinline__ void axis_tile(const AxisArgs& p, long long cta_tile,
 // Forward tau-FFT, propagator multiply, inverse tau-FFT, in one pass.
 template <class PL, int THREADS, class TW = TwShared>
 __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile, const TW& tw, float2* xch) {
-  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = col_tile_n(N);
+  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = ColTile<PL>::value;
   constexpr int TPC = tiles_per_cta_t<PL, THREADS>();
   static_assert(TPC >= 1 && TPC * T * TX == THREADS, "CTA must hold whole tiles");
   constexpr int R0 = fft_radix<PL, false>(0), RL = fft_radix<PL, false>(PL::NP - 1);
   constexpr int S0 = N / R0, SL = N / RL;
   const int lt = threadIdx.x % (T * TX), tl = threadIdx.x / (T * TX);
   const int tx = lt % TX, t = lt / TX;
-  const AxisTile<N, 2> a(p, cta_tile * TPC + tl, tx);
+  const AxisTile<N, 2, TX> a(p, cta_tile * TPC + tl, tx);
   const XchCol<TX> xc{xch + tl * N * TX, tx};
   float2 v[E];
 #pragma unroll
@@ -433,7 +439,8 @@ cudaError_t run_xpass(int nx, int nf, const XPassArgs& a, cudaStream_t s);
 cudaError_t run_axis_fft(int n, int axis, bool inv, const AxisArgs& a, cudaStream_t s);
 cudaError_t run_tpass_prop(int nt, const AxisArgs& a, cudaStream_t s);
 bool size_supported(int n);
-int col_tile_of(int n);
+int col_tile_of(int n);      // columns per tile of the y/tau FFT kernels
+int tau_col_tile_of(int n);  // columns per tile of the tau propagator kernel
 
 // misc kernels (k_misc.cu)
 // TMA tau-pass (k_tma.cu)
