@@ -34,6 +34,36 @@ METRIC = "grid-point·field·z-steps/sec and % of HBM roofline, plain vs batched
 UNIT = "grid-point·field·z-steps/s"
 KINDS = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
 FALLBACK_HBM_GBS = 6800.0
+# FP32 peak derived from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA)
+# at the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, 2070 MHz on this pool)
+SMS, FP32_LANES = 152, 128
+
+
+def _fp32_peak_tflops():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    mhz = 2070.0
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def alg_flops_per_point_field(kind, problem):
+    """Algorithmic FP32 flops per grid point per field of one launch.
+    FFTs count 5 n log2 n per transform of length n; complex multiply 6,
+    complex add 2.  The x-pass runs two RK4 half steps: per point, 4
+    right-hand sides (F=3: 6 complex products, F=2: 4), 3 stage inputs and
+    the weighted sum: 222 flops (F=3) or 148 (F=2) per RK4."""
+    import math
+    g, F = problem.grid, problem.nfields
+    rk4 = 222.0 if F == 3 else 148.0
+    if kind == "xpass_nl":
+        return 2 * 5 * math.log2(g.nx) + 2 * rk4 / F
+    if kind in ("ypass_fwd", "ypass_inv"):
+        return 5 * math.log2(g.ny)
+    if kind == "tpass_prop":
+        return 2 * 5 * math.log2(g.nt) + 6
+    return 0.0
 
 
 def _env_int(k, d):
@@ -376,23 +406,37 @@ def run_ours(args):
     ms_max = _max_over_ranks(dist, ms, dev)
     value = world * units_per_step * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel: algorithmic bytes = one read and one
-    # write of every field's state per launch (16 B per grid point per field)
+    # roofline of the dominant kernel.  HBM view: algorithmic bytes = one read
+    # and one write of every field's state per launch (16 B per grid point per
+    # field).  ALU view: algorithmic FP32 flops per launch against the FP32
+    # peak.  The bound reported is the one the kernel is closer to.
     main = int(np.argmax(kind_ms[:4]))
     alg_bytes = 16.0 * g.npoints * problem.nfields
     avg_s = kind_ms[main] / max(1, kind_n[main]) / 1e3
     peak, peak_kind = _peaks()
     achieved = alg_bytes / avg_s / 1e9
     traffic = _traffic(KINDS[main])
-    roofline = {"bound": "hbm", "kernel": KINDS[main], "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roof_hbm = {"bound": "hbm", "kernel": KINDS[main], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "alg_bytes_per_launch": alg_bytes}
+    fp_peak, mhz = _fp32_peak_tflops()
+    alg_flops = alg_flops_per_point_field(KINDS[main], problem) * g.npoints * problem.nfields
+    roof_alu = {"bound": "alu", "kernel": KINDS[main], "achieved": alg_flops / avg_s / 1e12, "peak": fp_peak,
+                "unit": "TFLOP/s", "frac": alg_flops / avg_s / 1e12 / fp_peak, "traffic": traffic,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz",
+                "alg_flops_per_launch": alg_flops}
+    roofline = roof_alu if roof_alu["frac"] > roof_hbm["frac"] else roof_hbm
+    roofline_other = roof_hbm if roofline is roof_alu else roof_alu
     total_k = float(np.sum(kind_ms))
+    def _rate(k, per_unit):
+        return float(per_unit / (kind_ms[k] / max(1, kind_n[k]) / 1e3)) if k < 4 and kind_n[k] else None
+
     kernels = {KINDS[k]: {"ms_total": float(kind_ms[k]), "launches": int(kind_n[k]),
                           "us_per_launch": float(1e3 * kind_ms[k] / max(1, kind_n[k])),
                           "share": float(kind_ms[k] / total_k) if total_k else 0.0,
-                          "GB_per_s_alg": float(alg_bytes / (kind_ms[k] / max(1, kind_n[k]) / 1e3) / 1e9)
-                          if k < 4 and kind_n[k] else None}
+                          "GB_per_s_alg": (_rate(k, alg_bytes) or 0) / 1e9 if k < 4 else None,
+                          "TFLOP_per_s_alg": (_rate(k, alg_flops_per_point_field(KINDS[k], problem) * g.npoints *
+                                                    problem.nfields) or 0) / 1e12 if k < 4 else None}
                for k in range(5)}
     step_alg_gbs = 16.0 * units_per_step * args.steps / (ms / 1e3) / 1e9
 
@@ -426,7 +470,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(problem, args), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": _config(problem, args), "roofline": roofline, "roofline_other_bound": roofline_other,
+            "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
             "step_hbm": {"alg_GB_per_s": step_alg_gbs, "alg_bytes_per_point_field_step": 16,
                          "moved_bytes_per_point_field_step_design": 64},
