@@ -216,17 +216,18 @@ def _max_over_ranks(dist, v, device):
     return float(t.item())
 
 
-def batched_form(dev, reps=2):
-    """The 64-run SHG sweep in one persistent graph-captured launch (after the
-    autotuner), against the same instances run one after another through the
+def batched_form(dev, reps=2, small=False):
+    """A sweep in one persistent graph-captured launch (after the autotuner),
+    against the same instances run one after another through the
     single-instance path.  Both are timed with CUDA events on their stream
-    and include the upload of the resident inputs."""
+    and include the upload of the resident inputs.  Default: the 64-run SHG
+    sweep; small=True: 256 runs of 32x32x64 SHG (200-800 steps each)."""
     import torch
 
     import paper_2609_08384_gb300 as br
     from paper_2609_08384_gb300 import workloads as wl
 
-    probs = wl.problems_batched()
+    probs = wl.problems_batched_small() if small else wl.problems_batched()
     ins = [[torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).to(dev) for a in wl.inputs_shg(p)]
            for p in probs]
     units = float(sum(p.grid.npoints * 2 * p.nz for p in probs))
@@ -274,7 +275,8 @@ def batched_form(dev, reps=2):
             "persistent_grid": info["grid"], "schedule_by_shape": sched, "tune_s": t_tune,
             "sequential_single_instance": {"value": units / (ms_seq / 1e3), "ms": ms_seq},
             "speedup_vs_sequential": ms_seq / ms_batch,
-            "workload": "64 SHG runs, grids {64^2x128, 96^2x192, 128^2x256}, 200-800 steps, 2 fields"}
+            "workload": ("256 SHG runs, 32^2x64, 200-800 steps, 2 fields" if small else
+                         "64 SHG runs, grids {64^2x128, 96^2x192, 128^2x256}, 200-800 steps, 2 fields")}
 
 
 def adjoint_form(dev):
@@ -460,6 +462,7 @@ def run_ours(args):
     forms = {"plain": value}
     if not args.no_forms:
         forms["batched"] = batched_form(dev)
+        forms["batched_small_grids"] = batched_form(dev, small=True)
         forms["adjoint"] = adjoint_form(dev)
 
     if rank != 0:

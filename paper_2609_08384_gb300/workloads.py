@@ -216,6 +216,19 @@ def problems_batched(count: int = 64, seed_index: int = 3) -> List[Problem]:
     return out
 
 
+def problems_batched_small(count: int = 256, seed_index: int = 5) -> List[Problem]:
+    """Many small SHG runs (32x32x64, window 400 um x 3.2 ps): dk ~ U[-200, 200]
+    1/m, L ~ U[0.5, 5] mm, nz ~ U{200..800}."""
+    rng = np.random.default_rng(SEED_BASE + seed_index)
+    out = []
+    for _ in range(count):
+        dk = float(rng.uniform(-200.0, 200.0))
+        length = float(rng.uniform(0.5, 5.0)) * MM
+        nz = int(rng.integers(200, 801))
+        out.append(problem_batch_member(32, 64, dk, length, nz))
+    return out
+
+
 def inputs_shg(p: Problem) -> List[np.ndarray]:
     a0 = peak_amplitude(1e13, N_F)
     f = focused_pulse(p.grid, p.fields[1], a0, 50 * UM, 200 * FS, p.length)
