@@ -67,7 +67,9 @@ typedef struct brahms_ctx brahms_ctx;
 brahms_status brahms_workspace_size(int nx, int ny, int nt, int nfields, size_t* bytes);
 
 /* Create a context.  nx, ny, nt: grid lengths, each one of 2,4,...,4096 or
- * 3*2^k for 6 <= 3*2^k <= 768 (else E_SIZE).  dx, dy [m], dt [s]: spacings > 0.
+ * 3*2^k for 6 <= 3*2^k <= 768; ny and nt may also be 1 (a 1D transverse
+ * grid, or a cw field with no tau extent: its linear step is the (kx, ky)
+ * multiply alone); else E_SIZE.  dx, dy [m], dt [s]: spacings > 0.
  * nfields: 2 (SH, F) or 3 (p, s, i); fp: nfields coefficient records.
  * d_eff [m/V]; dk [1/m]: constant mismatch Delta k = k_p - k_s - k_i (Eq. mismatch).
  * workspace: device memory of at least brahms_workspace_size() bytes, 256-byte
@@ -154,7 +156,8 @@ long long brahms_launch_count(const brahms_ctx* ctx);
 
 /* Set the fields (as brahms_set_fields), apply the phase (phi may be NULL),
  * propagate nz steps of dz with the profile dk, keep checkpoints, and return
- * J (weights: nfields entries).  Leaves the fields at z = nz dz.  Waits. */
+ * J (weights: nfields entries).  Leaves the fields at z = nz dz.  Waits.
+ * E_SIZE on grids with ny = 1 or nt = 1. */
 brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields, int dtype, int on_device,
                                      const double* phi, int phi_field, const double* dk, int nz, double dz,
                                      const double* weights, int checkpoint_interval, double* J);

@@ -32,10 +32,18 @@ const char* brahms_last_error(const brahms_ctx* ctx) {
   return ctx->err.c_str();
 }
 
+namespace {
+// x needs a transform of its own (it carries the nonlinear step); y and tau
+// may also have a single sample (a 1D transverse or a cw problem)
+bool grid_supported(int nx, int ny, int nt) {
+  return brahms::size_supported(nx) && (ny == 1 || brahms::size_supported(ny)) &&
+         (nt == 1 || brahms::size_supported(nt));
+}
+}  // namespace
+
 brahms_status brahms_workspace_size(int nx, int ny, int nt, int nfields, size_t* bytes) {
   if (!bytes || (nfields != 2 && nfields != 3)) return BRAHMS_E_ARG;
-  if (!brahms::size_supported(nx) || !brahms::size_supported(ny) || !brahms::size_supported(nt))
-    return BRAHMS_E_SIZE;
+  if (!grid_supported(nx, ny, nt)) return BRAHMS_E_SIZE;
   *bytes = make_layout(nx, ny, nt, nfields).total;
   return BRAHMS_OK;
 }
@@ -46,8 +54,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   if (!out || !fp) return BRAHMS_E_ARG;
   *out = nullptr;
   if (nfields != 2 && nfields != 3) return BRAHMS_E_ARG;
-  if (!brahms::size_supported(nx) || !brahms::size_supported(ny) || !brahms::size_supported(nt))
-    return BRAHMS_E_SIZE;
+  if (!grid_supported(nx, ny, nt)) return BRAHMS_E_SIZE;
   if (!(dx > 0) || !(dy > 0) || !(dt > 0) || !std::isfinite(dx) || !std::isfinite(dy) || !std::isfinite(dt) ||
       !std::isfinite(d_eff) || !std::isfinite(dk))
     return BRAHMS_E_ARG;
@@ -101,8 +108,8 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
-  if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
-  if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twt, nt, ctx->stream);
+  if (e == cudaSuccess && ny > 1) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
+  if (e == cudaSuccess && nt > 1) e = brahms::upload_twiddles(ctx->twt, nt, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
@@ -191,14 +198,16 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   }
   for (int i = 0; i < nz; ++i, ++j) {
     const double dkj = dk_of_step(ctx, j);
-    BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
-    if (ctx->use_tma)
+    if (ny > 1) BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
+    if (nt == 1)
+      BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_prop_pointwise(at, nf, ctx->stream); }));
+    else if (ctx->use_tma)
       BR_CK(launch(ctx, 2, 1, [&] {
         return brahms::run_tpass_prop_tma(nt, ctx->use_tma, ctx->tmap_state, at, ctx->dev_err, ctx->stream);
       }));
     else
       BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
-    BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ay, ctx->stream); }));
+    if (ny > 1) BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ay, ctx->stream); }));
     const bool last = (i == nz - 1);
     brahms::XPassArgs a = xargs(ctx, last ? brahms::XM_NL_LAST : brahms::XM_NL_MID, dz);
     a.phiB = phi;
@@ -276,8 +285,8 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   brahms::XPassArgs a = xargs(ctx, inv ? brahms::XM_INV : brahms::XM_FWD, 1.0);
   a.scale = (float)(1.0 / (double)ctx->npoints());
   BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(ctx->nx, ctx->nf, a, ctx->stream); }));
-  BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, inv, ay, ctx->stream); }));
-  BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, inv, at, ctx->stream); }));
+  if (ctx->ny > 1) BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, inv, ay, ctx->stream); }));
+  if (ctx->nt > 1) BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, inv, at, ctx->stream); }));
   BR_CK(cudaStreamSynchronize(ctx->stream));
   return BRAHMS_OK;
 }

@@ -72,7 +72,7 @@ struct InstDev {
   int nx, ny, nt, shape;
   int nz;
   double dz, dk;
-  float kh[2];
+  float kh[2], kh2[2];
   float scale, scale_lo;
   int n_x, n_y, n_t;      // items per pass type
   int g_x, g_y, g_t;      // CTA tiles per item (tile granularity)
@@ -173,8 +173,10 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
     p.rows = (long long)NXY * NT;
     p.tw = I.twx;
     p.dz = I.dz;
-    p.kh[0] = I.kh[0];
-    p.kh[1] = I.kh[1];
+    for (int f = 0; f < 2; ++f) {
+      p.kh[f] = I.kh[f];
+      p.kh2[f] = I.kh2[f];
+    }
     p.scale = 1.f;
     if (it.step < 0) {
       p.mode = XM_NL_FIRST;
@@ -433,6 +435,7 @@ brahms_status prepare(brahms_batch* b) {
       double k = kTwoPi * I.d_eff / (I.fp[f].n * I.fp[f].lambda);
       if (f == 0) k *= 0.5;
       d.kh[f] = (float)(k * 0.5 * I.dz);
+      d.kh2[f] = 0.5f * d.kh[f];
     }
     const double inv_n = 1.0 / (double)I.npoints();
     d.scale = (float)inv_n;

@@ -218,6 +218,7 @@ inline brahms::XPassArgs xargs(brahms_ctx* c, int mode, double dz) {
     double k = kappa(c, f);
     if (c->nf == 2 && f == 0) k *= 0.5;  // degenerate SHG: 1/2 on the SH equation
     a.kh[f] = (float)(k * 0.5 * dz);
+    a.kh2[f] = 0.5f * a.kh[f];
   }
   a.scale = 1.f;
   return a;
@@ -232,7 +233,8 @@ inline brahms::AxisArgs aargs(brahms_ctx* c, int axis, bool tau_prop = true) {
   a.nt = c->nt;
   a.fstride = c->npoints();
   const int n = axis == 1 ? c->ny : c->nt;
-  const int tx = (axis == 2 && tau_prop) ? brahms::tau_col_tile_of(n) : brahms::col_tile_of(n);
+  const int tx0 = (axis == 2 && tau_prop) ? brahms::tau_col_tile_of(n) : brahms::col_tile_of(n);
+  const int tx = tx0 > 0 ? tx0 : 1;  // an axis of length 1 has no tiles of its own
   a.xtiles = (c->nx + tx - 1) / tx;
   a.ntiles = (long long)c->nf * (axis == 1 ? c->nt : c->ny) * a.xtiles;
   a.tw = axis == 1 ? c->twy : c->twt;

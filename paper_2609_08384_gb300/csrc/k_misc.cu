@@ -129,6 +129,40 @@ static int grid_for(long long n) {
   return (int)(g > 152 * 16 ? 152 * 16 : (g < 1 ? 1 : g));
 }
 
+// ------------------------------------------------ pointwise linear step
+// The linear step of a grid without a tau extent (nt = 1, a cw field, or
+// any grid whose tau-transform is the identity): the multiply
+// P = (1 + Dx)(1 + Dy)(1 + Dt) / N of the tau-pass, element by element, with
+// the tau-pass's arithmetic, on the (kx, ky)-domain state.
+__global__ void prop_pointwise_kernel(const AxisArgs p, int nf) {
+  const long long plane = (long long)p.nx * p.ny;
+  const long long per_field = plane * p.nt;
+  const long long n = per_field * nf;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(i / per_field);
+    const long long r = i - (long long)f * per_field;
+    const int x = (int)(r % p.nx);
+    const int y = (int)((r / p.nx) % p.ny);
+    const int t = (int)(r / plane);
+    const float2 dx = p.px[f * p.nx + x], dy = p.py[f * p.ny + y];
+    float2 dxy = cadd(cadd(dx, dy), cmul(dx, dy));
+    float2 dt = p.pt[f * p.nt + t];
+    if (p.conj_p) {
+      dxy.y = -dxy.y;
+      dt.y = -dt.y;
+    }
+    float2* q = p.data + (long long)f * p.fstride + r;
+    float2 w = *q;
+    w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
+    *q = mul_one_plus(w, cadd(cadd(dxy, dt), cmul(dxy, dt)));
+  }
+}
+
+cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s) {
+  prop_pointwise_kernel<<<grid_for((long long)a.nx * a.ny * a.nt * nf), 256, 0, s>>>(a, nf);
+  return cudaPeekAtLastError();
+}
+
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s) {
   c128_to_c64_kernel<<<grid_for(n), 256, 0, s>>>(in, out, n);
   return cudaPeekAtLastError();

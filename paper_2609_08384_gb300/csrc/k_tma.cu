@@ -158,10 +158,9 @@ __global__ void __launch_bounds__(PL::T * TX, PL::T * TX <= 256 ? 2 : 1)
         const int kk = t + bb * T + r * SL;
         float2 dt = pt[kk];
         dt.y *= tsign;
-        const float2 d = cadd(cadd(dxy, dt), cmul(dxy, dt));
         float2 w = v[bb * RL + r];
         w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
-        v[bb * RL + r] = cadd(w, cmul(w, d));
+        v[bb * RL + r] = mul_one_plus(w, cadd(cadd(dxy, dt), cmul(dxy, dt)));
       }
     fft_run<PL, true, 0, XchCol<TX>, SyncBlock, TWA>(v, t, xc, tw);
     if (act) {

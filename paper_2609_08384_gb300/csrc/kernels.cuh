@@ -34,6 +34,7 @@ struct XPassArgs {
   double phiB, dkB;    // step whose second half is applied
   double dz;
   float kh[3];         // kappa_f * dz/2, including the 1/2 SH factor for 2 fields
+  float kh2[3];        // kh / 2 (exact)
   float scale;         // output scale for XM_INV
 };
 
@@ -94,8 +95,9 @@ __host__ __device__ constexpr int axis_smem_floats2() {
 
 // -------------------------------------------------------- nonlinear step
 // Right-hand sides of Eqs. CEp/CEs/CEi (3 fields p, s, i) or of the
-// degenerate SHG pair (SH, F), already multiplied by the step h:
-//   c[f] = i kappa_f h e^{-/+ i Phi(z)}  (minus for field 0)
+// degenerate SHG pair (SH, F), already multiplied by the step h, with
+//   c[f] = i kappa_f h e^{-/+ i Phi(z)}  (minus for field 0);
+// the adjoint's stage recomputation uses this form.
 template <int F>
 __device__ __forceinline__ void nl_rhs(const float2 (&a)[F], const float2* __restrict__ c,
                                        float2 (&k)[F]) {
@@ -109,35 +111,62 @@ __device__ __forceinline__ void nl_rhs(const float2 (&a)[F], const float2* __res
   }
 }
 
-// Classical RK4 over one half step; cs holds the coefficient sets at the
-// start, the midpoint and the end of the interval ([3][F]).
+// Stage right-hand sides in the form used by the forward half steps:
+// k_f = i (kappa_f h) m_f with e = e^{+i Phi(z_stage)} and
+//   F = 3: m_p = conj(e) A_s A_i,  m_s = e A_p conj(A_i),  m_i = e A_p conj(A_s)
+//   F = 2: m_SH = conj(e) A_F^2,   m_F = e A_SH conj(A_F)
+// (five complex products per stage for three fields instead of six; the
+// factor i kappa_f h goes into the stage updates' FMAs).
 template <int F>
-__device__ __forceinline__ void rk4(float2 (&a)[F], const float2* __restrict__ cs) {
-  float2 k[F], acc[F], t[F];
-  nl_rhs<F>(a, cs, k);
+__device__ __forceinline__ void nl_m(const float2 (&a)[F], float2 e, float2 (&m)[F]) {
+  if constexpr (F == 3) {
+    const float2 u = cmul(e, a[0]);
+    m[1] = cmulc(u, a[2]);
+    m[2] = cmulc(u, a[1]);
+    m[0] = cmulc(cmul(a[1], a[2]), e);
+  } else {
+    const float2 sq = make_float2(fmaf(a[1].x, a[1].x, -a[1].y * a[1].y), (a[1].x + a[1].x) * a[1].y);
+    m[0] = cmulc(sq, e);
+    m[1] = cmulc(cmul(e, a[0]), a[1]);
+  }
+}
+// a + i c m for a real c
+__device__ __forceinline__ float2 add_i_scaled(float2 a, float c, float2 m) {
+  return make_float2(fmaf(-c, m.y, a.x), fmaf(c, m.x, a.y));
+}
+
+// Classical RK4 over one half step h (Sec. 3.1): e3 holds e^{+i Phi} at the
+// start, the midpoint and the end of the interval; kh = kappa h and
+// kh2 = kh/2 per field.  Every stage and the final combination use the same
+// kh_f, and the 1/6 weight is common to all fields: field-dependent rounding
+// of the weights would break the Manley-Rowe balance the exact scheme keeps
+// and let the total energy drift step after step.
+template <int F>
+__device__ __forceinline__ void rk4(float2 (&a)[F], const float2* __restrict__ e3, const float* kh,
+                                    const float* kh2) {
+  float2 m[F], acc[F], t[F];
+  nl_m<F>(a, e3[0], m);
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    acc[f] = k[f];
-    t[f] = make_float2(fmaf(0.5f, k[f].x, a[f].x), fmaf(0.5f, k[f].y, a[f].y));
+    acc[f] = m[f];
+    t[f] = add_i_scaled(a[f], kh2[f], m[f]);
   }
-  nl_rhs<F>(t, cs + F, k);
+  const float2 emid = e3[1];
+  nl_m<F>(t, emid, m);
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    acc[f] = make_float2(fmaf(2.f, k[f].x, acc[f].x), fmaf(2.f, k[f].y, acc[f].y));
-    t[f] = make_float2(fmaf(0.5f, k[f].x, a[f].x), fmaf(0.5f, k[f].y, a[f].y));
+    acc[f] = make_float2(fmaf(2.f, m[f].x, acc[f].x), fmaf(2.f, m[f].y, acc[f].y));
+    t[f] = add_i_scaled(a[f], kh2[f], m[f]);
   }
-  nl_rhs<F>(t, cs + F, k);
+  nl_m<F>(t, emid, m);
 #pragma unroll
   for (int f = 0; f < F; ++f) {
-    acc[f] = make_float2(fmaf(2.f, k[f].x, acc[f].x), fmaf(2.f, k[f].y, acc[f].y));
-    t[f] = cadd(a[f], k[f]);
+    acc[f] = make_float2(fmaf(2.f, m[f].x, acc[f].x), fmaf(2.f, m[f].y, acc[f].y));
+    t[f] = add_i_scaled(a[f], kh[f], m[f]);
   }
-  nl_rhs<F>(t, cs + 2 * F, k);
+  nl_m<F>(t, e3[2], m);
 #pragma unroll
-  for (int f = 0; f < F; ++f) {
-    acc[f] = cadd(acc[f], k[f]);
-    a[f] = make_float2(fmaf(1.f / 6.f, acc[f].x, a[f].x), fmaf(1.f / 6.f, acc[f].y, a[f].y));
-  }
+  for (int f = 0; f < F; ++f) a[f] = add_i_scaled(a[f], kh[f], cscale(cadd(acc[f], m[f]), 1.f / 6.f));
 }
 
 // e^{-i Phi} with Phi in FP64, reduced to [-pi, pi] before the FP32 sincos.
@@ -149,9 +178,9 @@ __device__ __forceinline__ float2 phase_minus(double phi) {
   return make_float2(c, -s);
 }
 
-// Stage coefficients: sets 0..2 = second half of step B at z_B + dz/2,
-// z_B + 3dz/4, z_B + dz; sets 3..5 = first half of step A at z_A, z_A + dz/4,
-// z_A + dz/2.
+// Stage phase factors e^{+i Phi}: sets 0..2 = second half of step B at
+// z_B + dz/2, z_B + 3dz/4, z_B + dz; sets 3..5 = first half of step A at z_A,
+// z_A + dz/4, z_A + dz/2.
 template <int F>
 __device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef) {
   const int s = threadIdx.x;
@@ -160,12 +189,7 @@ __device__ __forceinline__ void nl_coefficients(const XPassArgs& p, float2* coef
     if (s < 3) phi = p.phiB + p.dkB * (0.5 * p.dz + 0.25 * p.dz * s);
     else phi = p.phiA + p.dkA * (0.25 * p.dz * (s - 3));
     const float2 em = phase_minus(phi);  // e^{-i Phi}
-#pragma unroll
-    for (int f = 0; f < F; ++f) {
-      // i * kh * e^{-i Phi} = kh (sin, cos) ; i * kh * e^{+i Phi} = kh (-sin, cos)
-      const float kh = p.kh[f];
-      coef[s * F + f] = f == 0 ? make_float2(-em.y * kh, em.x * kh) : make_float2(em.y * kh, em.x * kh);
-    }
+    coef[s] = make_float2(em.x, -em.y);
   }
 }
 
@@ -247,8 +271,8 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
       float2 a[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) a[f] = myrow[f * ROWS * PITCH + off];
-      if (mode != XM_NL_FIRST) rk4<F>(a, coef);
-      if (mode != XM_NL_LAST) rk4<F>(a, coef + 3 * F);
+      if (mode != XM_NL_FIRST) rk4<F>(a, coef, p.kh, p.kh2);
+      if (mode != XM_NL_LAST) rk4<F>(a, coef + 3, p.kh, p.kh2);
 #pragma unroll
       for (int f = 0; f < F; ++f) myrow[f * ROWS * PITCH + off] = a[f];
     }
@@ -297,6 +321,14 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
   __syncthreads();
   xpass_tile<NX, F, THREADS>(p, blockIdx.x, coef, rowbuf);
 }
+
+// w (1 + d) for a propagator factor in delta form: the small product w d is
+// formed first and w added with one rounding.  (Folding w into the FMA chain,
+// e.g. fma(w.x, d.x, fma(-w.y, d.y, w.x)), rounds w.x - w.y d.y before the
+// second-order term w.x (cos phi - 1) arrives; for small phases that term is
+// below half an ulp and is then always lost, so |1 + d| acts as
+// 1 + phi^2 / 2 and the energy grows step after step.)
+__device__ __forceinline__ float2 mul_one_plus(float2 w, float2 d) { return cadd(w, cmul(w, d)); }
 
 // ------------------------------------------------- strided-axis passes
 // AXIS 1: pencils along y (stride nx), tiles over (f, tau, x-tile).
@@ -387,10 +419,9 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
       const int k = t + b * T + r * SL;
       float2 dt = pt[k];
       dt.y *= tsign;
-      const float2 d = cadd(cadd(dxy, dt), cmul(dxy, dt));
       float2 w = v[b * RL + r];
       w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
-      v[b * RL + r] = cadd(w, cmul(w, d));
+      v[b * RL + r] = mul_one_plus(w, cadd(cadd(dxy, dt), cmul(dxy, dt)));
     }
   // the inverse's first pass reads exactly these positions
   fft_run<PL, true, 0, XchCol<TX>, SyncBlock, TW>(v, t, xc, tw);
@@ -461,6 +492,8 @@ struct TableArgs {
   double k[3], rho[3], delta[3], k2[3], k3[3], alpha[3];
 };
 cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s);
+// the linear step's multiply element by element (grids with nt = 1)
+cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s);
 cudaError_t run_energy(const float2* data, long long n, int nf, long long fstride, double* partial,
                        int nblocks, double* out, cudaStream_t s);
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
