@@ -89,6 +89,8 @@ def _load():
             lib.orc_propagate.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp]
             lib.orc_propagate.restype = ctypes.c_int
             lib.orc_energy.argtypes = [P(_Problem), vp, dp, dp]
+            lib.orc_power_trace.argtypes = [P(_Problem), vp, dp]
+            lib.orc_spectrum.argtypes = [P(_Problem), vp, dp]
             lib.orc_rk4_jvp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               vp, vp, vp, vp]
             lib.orc_rk4_vjp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -196,6 +198,22 @@ def energy(prob: _Problem, fields: Sequence[np.ndarray]):
     dp = ctypes.POINTER(ctypes.c_double)
     _load().orc_energy(ctypes.byref(prob), a.ctypes.data, e.ctypes.data_as(dp), ph.ctypes.data_as(dp))
     return e, ph
+
+
+def power_trace(prob: _Problem, fields: Sequence[np.ndarray]) -> np.ndarray:
+    """[nf, nt] temporal power [W] (orc_power_trace)."""
+    a = _stack(fields)
+    out = np.zeros((prob.nf, prob.nt))
+    _load().orc_power_trace(ctypes.byref(prob), a.ctypes.data, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def spectrum(prob: _Problem, fields: Sequence[np.ndarray]) -> np.ndarray:
+    """[nf, nt] energy per Omega bin [J], FFT order (orc_spectrum)."""
+    a = _stack(fields)
+    out = np.zeros((prob.nf, prob.nt))
+    _load().orc_spectrum(ctypes.byref(prob), a.ctypes.data, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
 
 
 def problem_from(p) -> _Problem:

@@ -412,6 +412,42 @@ void orc_energy(const orc_problem* pb, const cplx* fields, double* energy, doubl
   }
 }
 
+/* Temporal power trace (Sec. 6 power formula, integrated over the beam at
+ * each tau): power[f*nt + k] = 1/2 c eps0 n_f dx dy sum_{x,y} |A_f(x,y,tau_k)|^2 [W].
+ * sum_k power dt is the field energy of orc_energy.                          */
+void orc_power_trace(const orc_problem* pb, const cplx* fields, double* power) {
+  const int64_t plane = (int64_t)pb->nx * pb->ny, n = plane * pb->nt;
+  for (int f = 0; f < pb->nf; ++f) {
+    const double c = 0.5 * ORC_C0 * ORC_EPS0 * pb->f[f].n * pb->dx * pb->dy;
+    for (int k = 0; k < pb->nt; ++k) {
+      const cplx* a = fields + f * n + k * plane;
+      double s = 0.0;
+      for (int64_t i = 0; i < plane; ++i) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+      power[f * pb->nt + k] = c * s;
+    }
+  }
+}
+
+/* Energy spectrum over Omega, per bin of width 2 pi / (nt dt):
+ *   spectrum[f*nt + m] = 1/2 c eps0 n_f dx dy (dt / nt) sum_{x,y} |DFT_tau A_f|^2 (m),
+ * m in FFT order (Omega_m = orc_angular_freq(m, nt, dt)).  By Parseval the
+ * bins sum to the field energy.                                              */
+void orc_spectrum(const orc_problem* pb, const cplx* fields, double* spectrum) {
+  const int64_t plane = (int64_t)pb->nx * pb->ny, n = plane * pb->nt;
+  cplx* col = (cplx*)malloc(sizeof(cplx) * pb->nt);
+  for (int f = 0; f < pb->nf; ++f) {
+    const double c = 0.5 * ORC_C0 * ORC_EPS0 * pb->f[f].n * pb->dx * pb->dy * pb->dt / pb->nt;
+    for (int m = 0; m < pb->nt; ++m) spectrum[f * pb->nt + m] = 0.0;
+    for (int64_t i = 0; i < plane; ++i) {
+      for (int k = 0; k < pb->nt; ++k) col[k] = fields[f * n + k * plane + i];
+      orc_fft1d(col, pb->nt, -1);
+      for (int m = 0; m < pb->nt; ++m)
+        spectrum[f * pb->nt + m] += c * (creal(col[m]) * creal(col[m]) + cimag(col[m]) * cimag(col[m]));
+    }
+  }
+  free(col);
+}
+
 /* ======================================================================== */
 /* Discrete adjoint (reverse mode) of the split-step propagation.            */
 /*                                                                            */
