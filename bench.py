@@ -279,6 +279,52 @@ def batched_form(dev, reps=2, small=False):
                          "64 SHG runs, grids {64^2x128, 96^2x192, 128^2x256}, 200-800 steps, 2 fields")}
 
 
+def cw_form(dev, reps=2):
+    """cw focused SHG (nt = 1) at the Boyd-Kleinman optimum, 1024x1024, 1000
+    steps: the reduced-dimensional path (x-pass, y-passes, pointwise linear
+    step); CUDA events on the solver stream, resident inputs."""
+    import torch
+
+    import paper_2609_08384_gb300 as br
+    from paper_2609_08384_gb300 import workloads as wl
+
+    p = wl.problem_cw_shg()
+    ins = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.complex64)).to(dev) for a in wl.inputs_cw_shg(p)]
+    stream = torch.cuda.Stream(device=dev)
+    s = br.Solver(p.grid, p.fields, p.d_eff, p.dk, stream=stream, device=dev)
+    s.set_fields(ins)
+    s.propagate(20, p.dz)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        s.set_fields(ins)
+        s.propagate(p.nz, p.dz)
+    e1.record(stream)
+    s.sync()
+    ms = e0.elapsed_time(e1) / reps
+    e, _ = s.energy()
+    s.close()
+    units = float(p.grid.npoints * 2 * p.nz)
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms": ms, "shg_efficiency": float(e[0] / e.sum()),
+            "workload": "cw focused SHG 1024x1024 (nt = 1), w0 20 um, L = 2.84 b, dk b/2 = -0.57, 1000 steps"}
+
+
+def diagnostics_form(solver, problem, reps=3):
+    """Power trace plus spectrum of the resident OPG fields (each reads the
+    state once): wall time per call including the small device-to-host copy."""
+    import torch
+    solver.sync()
+    solver.diagnostics()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        solver.diagnostics()
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    nbytes = 2 * 8.0 * problem.grid.npoints * problem.nfields
+    return {"ms_per_call": ms, "alg_GB_per_s": nbytes / (ms / 1e3) / 1e9,
+            "workload": "power trace + tau spectrum of the 3 x 256x256x512 OPG state"}
+
+
 def adjoint_form(dev):
     """SHG efficiency gradient on 128x128x256 over 400 steps (256-entry spectral
     phase, 400-entry mismatch profile), sqrt(nz) checkpointing: the time of the
@@ -458,9 +504,12 @@ def run_ours(args):
     nbytes = g.npoints * problem.nfields * 8
     e2e = {"value": world * units_per_step * e2e_steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+    diag = diagnostics_form(solver, problem) if not args.no_forms else None
     solver.close()
     forms = {"plain": value}
     if not args.no_forms:
+        forms["diagnostics"] = diag
+        forms["cw_focused_shg"] = cw_form(dev)
         forms["batched"] = batched_form(dev)
         forms["batched_small_grids"] = batched_form(dev, small=True)
         forms["adjoint"] = adjoint_form(dev)

@@ -115,6 +115,17 @@ brahms_status brahms_sync(brahms_ctx* ctx);
  * normalised inverse (direction +1) to the state in place. */
 brahms_status brahms_transform(brahms_ctx* ctx, int direction);
 
+/* Diagnostics of the current fields (the Sec. 6 power formula resolved in
+ * tau or Omega); the state is not modified.  Each output holds nfields * nt
+ * doubles, [f][k], and may be NULL:
+ *   power[f][k]    = 1/2 c eps0 n_f dx dy sum_{x,y} |A_f(x, y, tau_k)|^2   [W]
+ *   spectrum[f][m] = 1/2 c eps0 n_f dx dy (dt / nt) sum_{x,y} |DFT_tau A_f|^2 (m)
+ *                    [J per bin of width 2 pi / (nt dt)], m in FFT order
+ *                    (Omega_m = 2 pi fftfreq(nt, dt)[m], the Nyquist bin negative).
+ * sum_k power dt and sum_m spectrum both equal the field energy.  Sums are
+ * FP64 (the spectrum's transform is FP32).  Waits for the stream. */
+brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectrum);
+
 /* Current propagation distance [m] and accumulated mismatch phase [rad]. */
 brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
 

@@ -57,6 +57,7 @@ SIGNATURES = {
     "brahms_sync": (_c.c_int, [_vp]),
     "brahms_transform": (_c.c_int, [_vp, _c.c_int]),
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
+    "brahms_diagnostics": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
     "brahms_launch_count": (_c.c_longlong, [_vp]),
     "brahms_set_option": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
@@ -214,6 +215,13 @@ class Solver:
         ph = np.zeros(self.nf)
         _check(self.ctx, load().brahms_energy(self.ctx, e.ctypes.data_as(_dp), ph.ctypes.data_as(_dp)))
         return e, ph
+
+    def diagnostics(self):
+        """(power [nf, nt] in W, spectrum [nf, nt] in J per Omega bin, FFT order)."""
+        p = np.zeros((self.nf, self.grid.nt))
+        sp = np.zeros((self.nf, self.grid.nt))
+        _check(self.ctx, load().brahms_diagnostics(self.ctx, p.ctypes.data_as(_dp), sp.ctypes.data_as(_dp)))
+        return p, sp
 
     def sync(self):
         _check(self.ctx, load().brahms_sync(self.ctx))

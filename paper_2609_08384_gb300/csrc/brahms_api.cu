@@ -106,6 +106,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->partial = (double*)(ctx->ws + ctx->L.partial);
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
   ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
+  ctx->diag_dev = (double*)(ctx->ws + ctx->L.diag);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
   if (e == cudaSuccess && ny > 1) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
@@ -288,6 +289,38 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   if (ctx->ny > 1) BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, inv, ay, ctx->stream); }));
   if (ctx->nt > 1) BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, inv, at, ctx->stream); }));
   BR_CK(cudaStreamSynchronize(ctx->stream));
+  return BRAHMS_OK;
+}
+
+brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectrum) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "no fields set");
+  if (!power && !spectrum) return BRAHMS_OK;
+  const int nt = ctx->nt, nf = ctx->nf;
+  double* pw = ctx->diag_dev;
+  double* sp = ctx->diag_dev + (size_t)nf * nt;
+  const bool want_power = power || nt == 1;
+  if (want_power)
+    BR_CK(launch(ctx, 4, 1, [&] {
+      return brahms::run_power_trace(ctx->state, ctx->nx, ctx->ny, nt, nf, ctx->npoints(), pw, ctx->stream);
+    }));
+  if (spectrum && nt > 1) {
+    const brahms::AxisArgs at = aargs(ctx, 2, false);
+    BR_CK(cudaMemsetAsync(sp, 0, sizeof(double) * nf * nt, ctx->stream));
+    BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_tau_spectrum(nt, at, sp, ctx->stream); }));
+  }
+  std::vector<double> h((size_t)2 * nf * nt);
+  BR_CK(cudaMemcpyAsync(h.data(), ctx->diag_dev, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  BR_CK(cudaStreamSynchronize(ctx->stream));
+  for (int f = 0; f < nf; ++f) {
+    const double c = 0.5 * kC0 * kEps0 * ctx->fp[f].n * ctx->dx * ctx->dy;
+    for (int k = 0; k < nt; ++k) {
+      const double p = c * h[(size_t)f * nt + k];
+      if (power) power[(size_t)f * nt + k] = p;
+      // nt = 1: the tau transform is the identity and the one bin holds P dt
+      if (spectrum) spectrum[(size_t)f * nt + k] = nt == 1 ? p * ctx->dt : c * ctx->dt / nt * h[(size_t)(nf + f) * nt + k];
+    }
+  }
   return BRAHMS_OK;
 }
 

@@ -23,7 +23,7 @@ constexpr int kKinds = 5;
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, total;
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, total;
 };
 
 inline Layout make_layout(int nx, int ny, int nt, int nf) {
@@ -45,6 +45,7 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.partial = take(sizeof(double) * kRedBlocks * nf);
   L.energy = take(sizeof(double) * nf);
   L.err = take(sizeof(int));
+  L.diag = take(sizeof(double) * 2 * nt * nf);
   L.total = off;
   return L;
 }
@@ -70,6 +71,7 @@ struct brahms_ctx {
   float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
   double *partial = nullptr, *energy_dev = nullptr;
   double* energy_host = nullptr;  // pinned, nf entries + the device error word
+  double* diag_dev = nullptr;     // diagnostics: power [nf][nt], spectrum [nf][nt]
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns

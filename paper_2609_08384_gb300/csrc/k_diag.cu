@@ -1,0 +1,165 @@
+// Diagnostics of the fields: the temporal power trace and the energy
+// spectrum over Omega (the Sec. 6 power formula resolved in tau or Omega).
+// Neither kernel writes the state.
+#include "kernels.cuh"
+
+namespace brahms {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// sum_{x,y} |A_f(x, y, tau_k)|^2 in FP64 for every (k, f): one CTA per plane
+__global__ void __launch_bounds__(256) power_trace_kernel(const float2* __restrict__ data, long long plane,
+                                                          int nt, long long fstride, double* out) {
+  const int k = blockIdx.x, f = blockIdx.y;
+  const float2* a = data + (long long)f * fstride + (long long)k * plane;
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < plane; i += blockDim.x) {
+    const float2 v = __ldcg(a + i);
+    s = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, s));
+  }
+  __shared__ double red[8];
+  s = warp_sum_d(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    v = warp_sum_d(v);
+    if (threadIdx.x == 0) out[f * nt + k] = v;
+  }
+}
+
+}  // namespace
+
+// sum_{x,y} |DFT_tau A_f|^2 (m) for every (m, f), added into out (zeroed by
+// the caller).  Each CTA walks a contiguous range of its tau-tiles (TX
+// neighbouring columns of one field and y), transforms them forward in
+// registers like the tau-pass, writes the squared moduli (FP32) to shared
+// memory and adds their sum over the tile's columns to per-thread FP64
+// accumulators of its bins; a change of field and the end of the range
+// flush them with one atomicAdd per bin.
+template <class PL>
+__global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
+    tau_spectrum_kernel(const AxisArgs p, long long range, double* out) {
+  constexpr int N = PL::N, E = PL::E, T = PL::T, TX = ColTile<PL>::value;
+  constexpr int GT = T * TX;                       // threads of one tile group
+  constexpr int THREADS = tiles_per_cta<PL>() * GT;
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int R0 = fft_radix<PL, false>(0), RL = fft_radix<PL, false>(PL::NP - 1);
+  constexpr int S0 = N / R0, SL = N / RL;
+  constexpr int BPT = (N + GT - 1) / GT;  // bins per thread
+  extern __shared__ float4 sm4[];
+  float2* xch = reinterpret_cast<float2*>(sm4);
+  if constexpr (tw_in_smem<PL>()) {
+    for (int i = threadIdx.x; i < tw_table_size<PL>(); i += THREADS) sm4[i] = p.tw[i];
+    __syncthreads();
+    xch = reinterpret_cast<float2*>(sm4 + tw_table_size<PL>());
+  }
+  const int lt = threadIdx.x % GT, tl = threadIdx.x / GT;
+  const int tx = lt % TX, t = lt / TX;
+  const XchCol<TX> xc{xch + tl * N * TX, tx};
+  // squared moduli of this group's tile, [TX][N + 1] (padded: the writes
+  // vary the column fastest, the reads the bin)
+  float* q = reinterpret_cast<float*>(xch + tl * N * TX);
+  double acc[BPT];
+#pragma unroll
+  for (int j = 0; j < BPT; ++j) acc[j] = 0.0;
+  int cur_f = -1;
+  const long long ctiles = (p.ntiles + TPC - 1) / TPC;
+  const long long first = (long long)blockIdx.x * range;
+  const long long last = first + range < ctiles ? first + range : ctiles;
+  for (long long ct = first; ct < last; ++ct) {
+    const long long tile = ct * TPC + tl;
+    const int ftile = tile < p.ntiles ? (int)((tile / p.xtiles) / p.ny) : cur_f;
+    if (ftile != cur_f) {
+      if (cur_f >= 0) {
+#pragma unroll
+        for (int j = 0; j < BPT; ++j)
+          if (lt + j * GT < N) atomicAdd(out + (long long)cur_f * N + lt + j * GT, acc[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < BPT; ++j) acc[j] = 0.0;
+      cur_f = ftile;
+    }
+    const AxisTile<N, 2, TX> a(p, tile, tx);
+    float2 v[E];
+#pragma unroll
+    for (int b = 0; b < E / R0; ++b)
+#pragma unroll
+      for (int r = 0; r < R0; ++r)
+        v[b * R0 + r] = a.act ? __ldcg(a.base + (t + b * T + r * S0) * a.stride) : make_float2(0.f, 0.f);
+    if constexpr (tw_in_smem<PL>()) fft_run<PL, false, 0, XchCol<TX>, SyncBlock, TwShared>(v, t, xc, TwShared{sm4});
+    else fft_run<PL, false, 0, XchCol<TX>, SyncBlock, TwGlobal>(v, t, xc, TwGlobal{p.tw});
+    __syncthreads();  // every read of the exchange space is done
+#pragma unroll
+    for (int b = 0; b < E / RL; ++b)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const float2 w = v[b * RL + r];
+        q[tx * (N + 1) + t + b * T + r * SL] = fmaf(w.x, w.x, w.y * w.y);
+      }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < BPT; ++j) {
+      const int k = lt + j * GT;
+      if (k < N) {
+        double s = 0.0;
+#pragma unroll
+        for (int c = 0; c < TX; ++c) s += (double)q[c * (N + 1) + k];
+        acc[j] += s;
+      }
+    }
+    __syncthreads();  // q is the next tile's exchange space
+  }
+  if (cur_f >= 0) {
+#pragma unroll
+    for (int j = 0; j < BPT; ++j)
+      if (lt + j * GT < N) atomicAdd(out + (long long)cur_f * N + lt + j * GT, acc[j]);
+  }
+}
+
+cudaError_t run_power_trace(const float2* data, int nx, int ny, int nt, int nf, long long fstride, double* out,
+                            cudaStream_t s) {
+  power_trace_kernel<<<dim3(nt, nf), 256, 0, s>>>(data, (long long)nx * ny, nt, fstride, out);
+  return cudaPeekAtLastError();
+}
+
+template <int N>
+static cudaError_t launch_spectrum(const AxisArgs& a, double* out, cudaStream_t s) {
+  using PL = FftPlan<N>;
+  constexpr int TPC = tiles_per_cta<PL>();
+  constexpr int THREADS = TPC * tile_threads<PL>();
+  const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(tau_spectrum_kernel<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const long long ctiles = (a.ntiles + TPC - 1) / TPC;
+  if (ctiles <= 0) return cudaSuccess;
+  const long long grid = ctiles < 2 * 152 ? ctiles : 2 * 152;
+  const long long range = (ctiles + grid - 1) / grid;
+  tau_spectrum_kernel<PL><<<(unsigned)((ctiles + range - 1) / range), THREADS, smem, s>>>(a, range, out);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_tau_spectrum(int nt, const AxisArgs& a, double* out, cudaStream_t s) {
+  switch (nt) {
+#define BRAHMS_SP_CASE(N) \
+  case N:                 \
+    return launch_spectrum<N>(a, out, s);
+    BRAHMS_FOR_EACH_SIZE(BRAHMS_SP_CASE)
+#undef BRAHMS_SP_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace brahms

@@ -494,6 +494,12 @@ struct TableArgs {
 cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s);
 // the linear step's multiply element by element (grids with nt = 1)
 cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s);
+// diagnostics (k_diag.cu): out[f nt + k] = sum_{x,y} |A_f(tau_k)|^2, and
+// out[f nt + m] += sum_{x,y} |DFT_tau A_f|^2 (m) (out zeroed by the caller;
+// a: tau-axis arguments without the propagator)
+cudaError_t run_power_trace(const float2* data, int nx, int ny, int nt, int nf, long long fstride, double* out,
+                            cudaStream_t s);
+cudaError_t run_tau_spectrum(int nt, const AxisArgs& a, double* out, cudaStream_t s);
 cudaError_t run_energy(const float2* data, long long n, int nf, long long fstride, double* partial,
                        int nblocks, double* out, cudaStream_t s);
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
