@@ -236,30 +236,58 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
   }
 }
 
-// Thread 0: find and claim the next runnable item.  Returns 1 with an item,
-// 0 when no instance has items left, -1 on timeout.
-__device__ int claim(const BatchArgs& b, int& inst, Item& it, unsigned long long t_start) {
+// Warp 0: find and claim the next runnable item.  The lanes look at 32
+// instances at a time (one L2 round trip per 32 instead of per instance);
+// the runnable candidate of lowest index -- the longest-first order -- takes
+// one atomicAdd on its counter, and on a lost race the next candidate is
+// tried.  The lane that wins writes the item to shared memory.  Returns, to
+// every lane, 1 with an item, 0 when no instance has items left, -1 on
+// timeout.
+__device__ int claim_warp(const BatchArgs& b, unsigned long long t_start, int* s_inst, Item* s_item) {
+  const int lane = threadIdx.x & 31;
   for (;;) {
     bool any_left = false;
-    for (int i = 0; i < b.ninst; ++i) {
-      const InstDev& I = b.inst[i];
-      const unsigned long long w = ld_relaxed64(b.next + i);
-      if ((long long)w >= I.total) continue;
-      any_left = true;
-      const Item peek = decode(I, (long long)w);
-      if (peek.q > 0 && ld_acquire(b.done + I.done_off + peek.q - 1) < pass_items(I, peek.q - 1)) continue;
-      const unsigned long long k = atomicAdd(b.next + i, 1ULL);
-      if ((long long)k >= I.total) continue;
-      it = decode(I, (long long)k);
-      if (it.q > 0) {
-        // the item may belong to the next pass when others claimed concurrently
-        while (ld_acquire(b.done + I.done_off + it.q - 1) < pass_items(I, it.q - 1)) {
-          if (gtimer() - t_start > b.timeout_ns) return -1;
-          __nanosleep(64);
+    for (int base = 0; base < b.ninst; base += 32) {
+      const int i = base + lane;
+      bool cand = false, left = false;
+      if (i < b.ninst) {
+        const InstDev& I = b.inst[i];
+        const unsigned long long w = ld_relaxed64(b.next + i);
+        if ((long long)w < I.total) {
+          left = true;
+          const Item peek = decode(I, (long long)w);
+          cand = peek.q == 0 || ld_acquire(b.done + I.done_off + peek.q - 1) >= pass_items(I, peek.q - 1);
         }
       }
-      inst = i;
-      return 1;
+      any_left = __any_sync(0xffffffffu, left) || any_left;
+      unsigned m = __ballot_sync(0xffffffffu, cand);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        int got = 0;
+        if (lane == src) {
+          const InstDev& I = b.inst[i];
+          const unsigned long long k = atomicAdd(b.next + i, 1ULL);
+          if ((long long)k < I.total) {
+            const Item it = decode(I, (long long)k);
+            got = 1;
+            if (it.q > 0) {
+              // the item may belong to the next pass when others claimed concurrently
+              while (ld_acquire(b.done + I.done_off + it.q - 1) < pass_items(I, it.q - 1)) {
+                if (gtimer() - t_start > b.timeout_ns) {
+                  got = -1;
+                  break;
+                }
+                __nanosleep(64);
+              }
+            }
+            *s_inst = i;
+            *s_item = it;
+          }
+        }
+        got = __shfl_sync(0xffffffffu, got, src);
+        if (got != 0) return got;
+        m &= m - 1;
+      }
     }
     if (!any_left) return 0;
     if (gtimer() - t_start > b.timeout_ns) return -1;
@@ -267,21 +295,26 @@ __device__ int claim(const BatchArgs& b, int& inst, Item& it, unsigned long long
   }
 }
 
+// Warp 0 claims the next item while warp 1 publishes the completion of the
+// previous one (fence + release), so the two round trips overlap.
 __global__ void __launch_bounds__(kBT, 2) batch_kernel(const BatchArgs b) {
   extern __shared__ float4 sm4[];
   __shared__ int s_inst, s_state;
   __shared__ Item s_item;
+  long long prev = -1;  // completion counter of the previous item (thread 32)
   for (;;) {
-    if (threadIdx.x == 0) {
-      int inst = 0;
-      Item it{};
+    if (threadIdx.x < 32) {
       // the timeout covers one claim: the time a CTA may wait for runnable work
-      const int r = claim(b, inst, it, gtimer());
-      if (r < 0) atomicExch(b.status, (int)BRAHMS_E_TIMEOUT);
-      if (r > 0 && ld_acquire(reinterpret_cast<const unsigned int*>(b.status)) != 0) s_state = 0;
-      else s_state = r;
-      s_inst = inst;
-      s_item = it;
+      const int r = claim_warp(b, gtimer(), &s_inst, &s_item);
+      __syncwarp();
+      if (threadIdx.x == 0) {
+        if (r < 0) atomicExch(b.status, (int)BRAHMS_E_TIMEOUT);
+        if (r > 0 && ld_acquire(reinterpret_cast<const unsigned int*>(b.status)) != 0) s_state = 0;
+        else s_state = r;
+      }
+    } else if (threadIdx.x == 32 && prev >= 0) {
+      __threadfence();
+      red_release_add(b.done + prev, 1u);
     }
     __syncthreads();
     if (s_state <= 0) break;
@@ -293,11 +326,8 @@ __global__ void __launch_bounds__(kBT, 2) batch_kernel(const BatchArgs b) {
       case 2: run_item<2>(I, it, sm4); break;
       default: run_item<3>(I, it, sm4); break;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      red_release_add(b.done + I.done_off + it.q, 1u);
-    }
+    __syncthreads();  // the item's stores are issued; s_item may be rewritten
+    prev = I.done_off + it.q;
   }
 }
 
