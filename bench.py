@@ -170,9 +170,21 @@ def cpu_baseline(problem, inputs, nz_sample=1):
     oracle.propagate(prob, inputs, nz_sample, problem.dz, problem.dk)
     dt = time.perf_counter() - t0
     units = problem.grid.npoints * problem.nfields * nz_sample
-    return {"value": units / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
-            "sample": f"{nz_sample} split step(s) of the {problem.name} workload "
-                      f"({problem.nfields} fields, FP64), {dt:.1f} s"}
+    out = {"value": units / dt, "unit": UNIT, "cores": int(cores), "kind": "oracle",
+           "sample": f"{nz_sample} split step(s) of the {problem.name} workload "
+                     f"({problem.nfields} fields, FP64), {dt:.1f} s"}
+    # one thread, on a bounded sample: one step of the 128x128x256 SFG grid
+    from paper_2609_08384_gb300 import workloads as wl
+    ps = wl.problem_sfg()
+    ins = [np.ascontiguousarray(a, dtype=np.complex64).astype(np.complex128) for a in wl.inputs_sfg(ps)]
+    oracle.set_threads(1)
+    t0 = time.perf_counter()
+    oracle.propagate(oracle.problem_from(ps), ins, 1, ps.dz, ps.dk)
+    dt1 = time.perf_counter() - t0
+    oracle.set_threads(cores)
+    out["one_thread"] = {"value": ps.grid.npoints * ps.nfields / dt1, "unit": UNIT, "cores": 1,
+                         "sample": f"1 split step of the {ps.name} workload (3 fields, FP64), {dt1:.1f} s"}
+    return out
 
 
 def make_workload(name):
@@ -275,6 +287,7 @@ def batched_form(dev, reps=2, small=False):
             "persistent_grid": info["grid"], "schedule_by_shape": sched, "tune_s": t_tune,
             "sequential_single_instance": {"value": units / (ms_seq / 1e3), "ms": ms_seq},
             "speedup_vs_sequential": ms_seq / ms_batch,
+            "moved_GB_per_s_design": 64.0 * units / (ms_batch / 1e3) / 1e9,
             "workload": ("256 SHG runs, 32^2x64, 200-800 steps, 2 fields" if small else
                          "64 SHG runs, grids {64^2x128, 96^2x192, 128^2x256}, 200-800 steps, 2 fields")}
 
@@ -526,7 +539,8 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "kernels": kernels,
             "step_hbm": {"alg_GB_per_s": step_alg_gbs, "alg_bytes_per_point_field_step": 16,
-                         "moved_bytes_per_point_field_step_design": 64},
+                         "moved_bytes_per_point_field_step_design": 64,
+                         "moved_GB_per_s": 64.0 * value / 1e9, "moved_frac_of_peak": 64.0 * value / 1e9 / peak},
             "forms": forms}
     print(json.dumps(line), flush=True)
     return 0
