@@ -89,6 +89,9 @@ def _load():
             lib.orc_propagate.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp]
             lib.orc_propagate.restype = ctypes.c_int
             lib.orc_energy.argtypes = [P(_Problem), vp, dp, dp]
+            lib.orc_propagate_map.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp,
+                                              ctypes.c_double, dp]
+            lib.orc_propagate_map.restype = ctypes.c_int
             lib.orc_power_trace.argtypes = [P(_Problem), vp, dp]
             lib.orc_spectrum.argtypes = [P(_Problem), vp, dp]
             lib.orc_rk4_jvp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -198,6 +201,22 @@ def energy(prob: _Problem, fields: Sequence[np.ndarray]):
     dp = ctypes.POINTER(ctypes.c_double)
     _load().orc_energy(ctypes.byref(prob), a.ctypes.data, e.ctypes.data_as(dp), ph.ctypes.data_as(dp))
     return e, ph
+
+
+def propagate_map(prob: _Problem, fields: Sequence[np.ndarray], nz: int, dz: float, dk, dk_map: np.ndarray,
+                  phi0: float = 0.0, z0: float = 0.0, check: bool = True):
+    """propagate() with a transverse mismatch map dk_map[ny, nx] [1/m] added to
+    every step's dk; z0 is the distance from the start of the crystal."""
+    a = _stack(fields)
+    dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
+    m = np.ascontiguousarray(dk_map, dtype=np.float64).reshape(prob.ny, prob.nx)
+    phi = ctypes.c_double(phi0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = _load().orc_propagate_map(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), dks.ctypes.data_as(dp),
+                                   ctypes.byref(phi), float(z0), m.ctypes.data_as(dp))
+    if check and rc != 0:
+        raise FloatingPointError("oracle: non-finite fields (dz too large)")
+    return a, phi.value
 
 
 def power_trace(prob: _Problem, fields: Sequence[np.ndarray]) -> np.ndarray:

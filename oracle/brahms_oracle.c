@@ -363,6 +363,47 @@ void orc_nonlinear_step(const orc_problem* pb, cplx* fields, double phi_a, doubl
   parallel_for((int64_t)pb->nx * pb->ny * pb->nt, nl_range, &j);
 }
 
+/* N(h) with a transverse mismatch map (f2 of the build's scope):
+ * Delta k(x, y, z) = dk + dk_map[y nx + x] on this step, so at every point
+ *   Phi(x, y, z_a + s) = phi_a + dk_map(x, y) z_a + (dk + dk_map(x, y)) s,
+ * z_a measured from the start of the crystal; each point then takes the
+ * RK4 of orc_rk4_point with its own phase origin and slope.                 */
+typedef struct {
+  const orc_problem* pb;
+  cplx* fields;
+  double kap[3];
+  double phi_a, dk, h, z_a;
+  const double* dk_map;
+} nlm_job;
+
+static void nlm_range(void* p, int64_t b, int64_t e) {
+  nlm_job* j = (nlm_job*)p;
+  const int64_t plane = (int64_t)j->pb->nx * j->pb->ny;
+  const int64_t n = plane * j->pb->nt;
+  const int nf = j->pb->nf;
+  for (int64_t i = b; i < e; ++i) {
+    const double m = j->dk_map[i % plane];
+    cplx A[3];
+    for (int f = 0; f < nf; ++f) A[f] = j->fields[f * n + i];
+    orc_rk4_point(nf, j->kap, j->phi_a + m * j->z_a, j->dk + m, j->h, A);
+    for (int f = 0; f < nf; ++f) j->fields[f * n + i] = A[f];
+  }
+}
+
+void orc_nonlinear_step_map(const orc_problem* pb, cplx* fields, double phi_a, double dk, double h, double z_a,
+                            const double* dk_map) {
+  nlm_job j;
+  j.pb = pb;
+  j.fields = fields;
+  for (int f = 0; f < pb->nf; ++f) j.kap[f] = orc_kappa(pb, f);
+  j.phi_a = phi_a;
+  j.dk = dk;
+  j.h = h;
+  j.z_a = z_a;
+  j.dk_map = dk_map;
+  parallel_for((int64_t)pb->nx * pb->ny * pb->nt, nlm_range, &j);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Split-step propagation (Eq. expon):  N(dz/2)  L(dz)  N(dz/2)  per step.     */
 /* ------------------------------------------------------------------------ */
@@ -378,6 +419,25 @@ int orc_propagate(const orc_problem* pb, cplx* fields, int nz, double dz, const 
     orc_nonlinear_step(pb, fields, ph, dk, 0.5 * dz);
     orc_linear_step(pb, fields, dz);
     orc_nonlinear_step(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz);
+    ph += dk * dz;
+  }
+  *phi = ph;
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt * pb->nf;
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(creal(fields[i])) || !isfinite(cimag(fields[i]))) return 5;
+  return 0;
+}
+
+/* As orc_propagate with the transverse mismatch map dk_map[ny][nx] added to
+ * every step's dk; z0 is the distance from the start of the crystal.        */
+int orc_propagate_map(const orc_problem* pb, cplx* fields, int nz, double dz, const double* dk_steps, double* phi,
+                      double z0, const double* dk_map) {
+  double ph = *phi;
+  for (int j = 0; j < nz; ++j) {
+    const double dk = dk_steps[j], zj = z0 + j * dz;
+    orc_nonlinear_step_map(pb, fields, ph, dk, 0.5 * dz, zj, dk_map);
+    orc_linear_step(pb, fields, dz);
+    orc_nonlinear_step_map(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz, zj + 0.5 * dz, dk_map);
     ph += dk * dz;
   }
   *phi = ph;

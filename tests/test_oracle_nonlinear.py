@@ -220,3 +220,55 @@ def test_nonfinite_is_reported():
     with pytest.raises(FloatingPointError):
         # absurd step: |Delta A| >> |A| blows up (Sec. 3.2)
         oracle.propagate(prob, [_uniform(PW, 0), _uniform(PW, 1e12)], 40, 1.0, 0.0)
+
+
+# ------------------------------------------------- transverse mismatch map
+def _no_walkoff_shg():
+    return [FieldParams(LAM_SH, N_SH, k2=1e-25), FieldParams(LAM_F, N_F, k2=2e-25)]
+
+
+def test_map_columns_follow_undepleted_sinc():
+    """Delta k(x) = dk + m(x) (a fan-out grating): with a uniform weak F and a
+    1 m grid spacing (diffraction and walk-off are negligible), every column
+    follows its own plane-wave sinc law with its own mismatch."""
+    g = Grid(8, 2, 2, 1.0, 1.0, 10 * FS)
+    prob = oracle.make_problem(g, _no_walkoff_shg(), D_EFF)
+    kSH = 2 * math.pi * D_EFF / (N_SH * LAM_SH)
+    a = 1.0 + 0.5j
+    L, nz, dk = 3 * MM, 300, 150.0
+    m = np.tile(np.linspace(-2000.0, 2000.0, 8), (2, 1))
+    out, _ = oracle.propagate_map(prob, [_uniform(g, 0), _uniform(g, a)], nz, L / nz, dk, m)
+    for x in range(8):
+        d = dk + m[0, x]
+        s = math.sin(d * L / 2) / (d * L / 2) if d != 0 else 1.0
+        expect = 1j * (kSH / 2) * a * a * L * np.exp(-1j * d * L / 2) * s
+        assert abs(out[0, 1, 1, x] - expect) / abs(kSH * a * a * L) < 1e-9
+
+
+def test_uniform_map_equals_scalar_mismatch():
+    """A map that is the same everywhere is the same as adding it to dk."""
+    g = Grid(8, 6, 12, 5 * UM, 5 * UM, 30 * FS)
+    fields = [FieldParams(1064e-9, 2.15, delta=1e-10, k2=2e-25, rho=2e-3),
+              FieldParams(1450e-9, 2.14, k2=1e-25),
+              FieldParams(1.0 / (1.0 / 1064e-9 - 1.0 / 1450e-9), 2.08, delta=-1e-10, rho=1e-3)]
+    prob = oracle.make_problem(g, fields, D_EFF)
+    rng = np.random.default_rng(17)
+    init = [3e8 * (rng.standard_normal((12, 6, 8)) + 1j * rng.standard_normal((12, 6, 8))) for _ in range(3)]
+    prof = rng.normal(0.0, 300.0, 10)
+    ref, phr = oracle.propagate(prob, init, 10, 7 * UM, prof + 450.0)
+    got, phg = oracle.propagate_map(prob, init, 10, 7 * UM, prof, np.full((6, 8), 450.0))
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    assert phg == pytest.approx(phr - 450.0 * 10 * 7 * UM, rel=1e-12)
+
+
+def test_map_split_calls_equal_one_call():
+    """z0 carries the distance from the crystal start across calls."""
+    g = Grid(8, 4, 8, 5 * UM, 5 * UM, 30 * FS)
+    prob = oracle.make_problem(g, _no_walkoff_shg(), D_EFF)
+    rng = np.random.default_rng(3)
+    init = [1e8 * (rng.standard_normal((8, 4, 8)) + 1j * rng.standard_normal((8, 4, 8))) for _ in range(2)]
+    m = rng.normal(0.0, 500.0, (4, 8))
+    one, _ = oracle.propagate_map(prob, init, 12, 6 * UM, 80.0, m)
+    a, ph = oracle.propagate_map(prob, init, 5, 6 * UM, 80.0, m)
+    two, _ = oracle.propagate_map(prob, list(a), 7, 6 * UM, 80.0, m, phi0=ph, z0=5 * 6 * UM)
+    assert np.linalg.norm(two - one) / np.linalg.norm(one) < 1e-13
