@@ -323,6 +323,38 @@ def cw_form(dev, reps=2):
             "workload": "cw focused SHG 1024x1024 (nt = 1), w0 20 um, L = 2.84 b, dk b/2 = -0.57, 1000 steps"}
 
 
+def dk_map_form(dev, inputs, nz=200):
+    """OPG with a fan-out mismatch map (dk(x) = 2000 1/m per 100 um of x):
+    the per-point stage phases of the x-pass; CUDA events on the solver stream."""
+    import torch
+
+    import paper_2609_08384_gb300 as br
+    from paper_2609_08384_gb300 import workloads as wl
+
+    p = wl.problem_opg()
+    x, _, _ = p.grid.axes()
+    m = np.tile(2e7 * x, (p.grid.ny, 1))
+    stream = torch.cuda.Stream(device=dev)
+    s = br.Solver(p.grid, p.fields, p.d_eff, p.dk, stream=stream, device=dev)
+    s.set_dk_map(m)
+    s.set_fields(inputs)
+    s.propagate(10, p.dz)
+    s.sync()
+    s.timing(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.propagate(nz, p.dz)
+    e1.record(stream)
+    s.sync()
+    ms = e0.elapsed_time(e1)
+    kind_ms, kind_n = s.timing(False)
+    s.close()
+    units = float(p.grid.npoints * p.nfields * nz)
+    return {"value": units / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "xpass_us_per_launch": float(kind_ms[0] / max(1, kind_n[0]) * 1e3),
+            "workload": f"OPG 256x256x512, {nz} steps, fan-out mismatch map dk(x) = 2e7 x (1/m)"}
+
+
 def diagnostics_form(solver, problem, reps=3):
     """Power trace plus spectrum of the resident OPG fields (each reads the
     state once): wall time per call including the small device-to-host copy."""
@@ -523,6 +555,8 @@ def run_ours(args):
     if not args.no_forms:
         forms["diagnostics"] = diag
         forms["cw_focused_shg"] = cw_form(dev)
+        if problem.name.startswith("opg"):
+            forms["dk_map"] = dk_map_form(dev, dev_in)
         forms["batched"] = batched_form(dev)
         forms["batched_small_grids"] = batched_form(dev, small=True)
         forms["adjoint"] = adjoint_form(dev)

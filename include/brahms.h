@@ -115,6 +115,15 @@ brahms_status brahms_sync(brahms_ctx* ctx);
  * normalised inverse (direction +1) to the state in place. */
 brahms_status brahms_transform(brahms_ctx* ctx, int direction);
 
+/* Transverse mismatch map (the mismatch field of a fan-out grating or of a
+ * static dephasing profile): dk_map[ny][nx] in 1/m, x fastest, is added to
+ * every step's Delta k, so the nonlinear step's phase becomes
+ *   Phi(x, y, z) = Phi_j + Delta k_j (z - z_j) + dk_map(x, y) z,
+ * z measured from the last brahms_set_fields.  The library copies the map;
+ * NULL removes it.  E_ARG for non-finite entries.  The adjoint refuses a
+ * context with a map (E_STATE). */
+brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
+
 /* Diagnostics of the current fields (the Sec. 6 power formula resolved in
  * tau or Omega); the state is not modified.  Each output holds nfields * nt
  * doubles, [f][k], and may be NULL:

@@ -58,6 +58,7 @@ SIGNATURES = {
     "brahms_transform": (_c.c_int, [_vp, _c.c_int]),
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_diagnostics": (_c.c_int, [_vp, _dp, _dp]),
+    "brahms_set_dk_map": (_c.c_int, [_vp, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
     "brahms_launch_count": (_c.c_longlong, [_vp]),
     "brahms_set_option": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
@@ -215,6 +216,14 @@ class Solver:
         ph = np.zeros(self.nf)
         _check(self.ctx, load().brahms_energy(self.ctx, e.ctypes.data_as(_dp), ph.ctypes.data_as(_dp)))
         return e, ph
+
+    def set_dk_map(self, dk_map):
+        """Transverse mismatch map [ny, nx] in 1/m added to every step's dk; None removes it."""
+        if dk_map is None:
+            _check(self.ctx, load().brahms_set_dk_map(self.ctx, None))
+            return
+        m = np.ascontiguousarray(dk_map, dtype=np.float64).reshape(self.grid.ny, self.grid.nx)
+        _check(self.ctx, load().brahms_set_dk_map(self.ctx, m.ctypes.data_as(_dp)))
 
     def diagnostics(self):
         """(power [nf, nt] in W, spectrum [nf, nt] in J per Omega bin, FFT order)."""

@@ -89,6 +89,7 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
                                      const double* weights, int checkpoint_interval, double* J) {
   if (!ctx) return BRAHMS_E_ARG;
   if (ctx->ny < 2 || ctx->nt < 2) return fail(ctx, BRAHMS_E_SIZE, "the adjoint needs ny >= 2 and nt >= 2");
+  if (ctx->have_map) return fail(ctx, BRAHMS_E_STATE, "the adjoint does not take a transverse mismatch map");
   if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
     return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
   if (phi && (phi_field < 0 || phi_field >= ctx->nf)) return fail(ctx, BRAHMS_E_ARG, "phi_field out of range");

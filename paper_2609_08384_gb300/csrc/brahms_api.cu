@@ -107,6 +107,8 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
   ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
   ctx->diag_dev = (double*)(ctx->ws + ctx->L.diag);
+  ctx->dkmap_dev = (double*)(ctx->ws + ctx->L.dkmap);
+  ctx->emap_dev = (float2*)(ctx->ws + ctx->L.emap);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
   if (e == cudaSuccess && ny > 1) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
@@ -191,10 +193,13 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   const brahms::AxisArgs at = aargs(ctx, 2);
   double phi = ctx->phi;  // Phi(z_j) of the current step j
   long long j = ctx->step;
+  const double z0 = ctx->z;
   {
     brahms::XPassArgs a = xargs(ctx, brahms::XM_NL_FIRST, dz);
     a.phiA = phi;
     a.dkA = dk_of_step(ctx, j);
+    s = enqueue_map_tables(ctx, 0.0, 0.0, z0, a.phiA, a.dkA, z0, dz);
+    if (s != BRAHMS_OK) return s;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, a, ctx->stream); }));
   }
   for (int i = 0; i < nz; ++i, ++j) {
@@ -216,6 +221,8 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
     phi += dkj * dz;
     a.phiA = phi;
     a.dkA = dk_of_step(ctx, j + 1);
+    s = enqueue_map_tables(ctx, a.phiB, a.dkB, z0 + i * dz, a.phiA, a.dkA, z0 + (i + 1) * dz, dz);
+    if (s != BRAHMS_OK) return s;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, a, ctx->stream); }));
   }
   ctx->phi = phi;
@@ -289,6 +296,21 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   if (ctx->ny > 1) BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, inv, ay, ctx->stream); }));
   if (ctx->nt > 1) BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_axis_fft(ctx->nt, 2, inv, at, ctx->stream); }));
   BR_CK(cudaStreamSynchronize(ctx->stream));
+  return BRAHMS_OK;
+}
+
+brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (!dk_map) {
+    ctx->have_map = false;
+    return BRAHMS_OK;
+  }
+  const size_t n = (size_t)ctx->nx * ctx->ny;
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(dk_map[i])) return fail(ctx, BRAHMS_E_ARG, "dk_map has non-finite entries");
+  BR_CK(cudaMemcpyAsync(ctx->dkmap_dev, dk_map, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  BR_CK(cudaStreamSynchronize(ctx->stream));
+  ctx->have_map = true;
   return BRAHMS_OK;
 }
 

@@ -23,7 +23,7 @@ constexpr int kKinds = 5;
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, total;
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, dkmap, emap, total;
 };
 
 inline Layout make_layout(int nx, int ny, int nt, int nf) {
@@ -46,6 +46,8 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.energy = take(sizeof(double) * nf);
   L.err = take(sizeof(int));
   L.diag = take(sizeof(double) * 2 * nt * nf);
+  L.dkmap = take(sizeof(double) * nx * ny);
+  L.emap = take(sizeof(float2) * 4 * nx * ny);
   L.total = off;
   return L;
 }
@@ -72,6 +74,9 @@ struct brahms_ctx {
   double *partial = nullptr, *energy_dev = nullptr;
   double* energy_host = nullptr;  // pinned, nf entries + the device error word
   double* diag_dev = nullptr;     // diagnostics: power [nf][nt], spectrum [nf][nt]
+  double* dkmap_dev = nullptr;    // transverse mismatch map [ny][nx] (1/m)
+  float2* emap_dev = nullptr;     // its stage phase factors for one x-pass [4][ny][nx]
+  bool have_map = false;
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns
@@ -223,7 +228,30 @@ inline brahms::XPassArgs xargs(brahms_ctx* c, int mode, double dz) {
     a.kh2[f] = 0.5f * a.kh[f];
   }
   a.scale = 1.f;
+  a.ny = c->ny;
+  a.emap = c->have_map ? c->emap_dev : nullptr;
   return a;
+}
+
+// Stage phase factors of the next x-pass under the mismatch map: B applies
+// the second half of the step that starts at distance zB (mismatch phase
+// phiB, mismatch dkB), A the first half of the step that starts at zA.
+inline brahms_status enqueue_map_tables(brahms_ctx* ctx, double phiB, double dkB, double zB, double phiA,
+                                        double dkA, double zA, double dz) {
+  if (!ctx->have_map) return BRAHMS_OK;
+  brahms::MapArgs m{};
+  m.dkmap = ctx->dkmap_dev;
+  m.emap = ctx->emap_dev;
+  m.nxy = (long long)ctx->nx * ctx->ny;
+  m.phiB = phiB;
+  m.dkB = dkB;
+  m.zB = zB;
+  m.phiA = phiA;
+  m.dkA = dkA;
+  m.zA = zA;
+  m.dz = dz;
+  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_map_tables(m, ctx->stream); }));
+  return BRAHMS_OK;
 }
 
 // axis 1: y-pass; axis 2 with tau_prop: tau propagator; axis 2 without: tau FFT only

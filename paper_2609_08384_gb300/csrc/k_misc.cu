@@ -55,6 +55,30 @@ __global__ void prop_tables_kernel(const TableArgs a) {
   a.pt[f * a.nt + m] = delta_phase(ph, expm1(-0.5 * a.alpha[f] * a.dz));
 }
 
+// ---------------------------------------------- mismatch-map tables
+__device__ __forceinline__ float2 phase_plus(double phi) {
+  const float2 em = phase_minus(phi);
+  return make_float2(em.x, -em.y);
+}
+
+__global__ void map_tables_kernel(const MapArgs a) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.nxy;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double m = a.dkmap[i];
+    a.emap[i] = phase_plus(a.phiB + a.dkB * 0.5 * a.dz + m * (a.zB + 0.5 * a.dz));
+    a.emap[a.nxy + i] = phase_plus((a.dkB + m) * 0.25 * a.dz);
+    a.emap[2 * a.nxy + i] = phase_plus(a.phiA + m * a.zA);
+    a.emap[3 * a.nxy + i] = phase_plus((a.dkA + m) * 0.25 * a.dz);
+  }
+}
+
+cudaError_t run_map_tables(const MapArgs& a, cudaStream_t s) {
+  long long g = (a.nxy + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  map_tables_kernel<<<(unsigned)g, 256, 0, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
 cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s) {
   const int n = (a.nx + a.ny + a.nt) * a.nf;
   prop_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(a);

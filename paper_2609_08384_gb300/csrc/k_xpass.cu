@@ -3,21 +3,27 @@
 
 namespace brahms {
 
-template <int NX, int F>
-static cudaError_t launch_x(const XPassArgs& a, cudaStream_t s) {
+template <int NX, int F, bool MAP>
+static cudaError_t launch_x_variant(const XPassArgs& a, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(xpass_kernel<NX, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(xpass_kernel<NX, F, MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   const long long grid = (a.rows + ROWS - 1) / ROWS;
   if (grid <= 0) return cudaSuccess;
-  xpass_kernel<NX, F><<<(unsigned)grid, THREADS, smem, s>>>(a);
+  xpass_kernel<NX, F, MAP><<<(unsigned)grid, THREADS, smem, s>>>(a);
   return cudaPeekAtLastError();
+}
+
+template <int NX, int F>
+static cudaError_t launch_x(const XPassArgs& a, cudaStream_t s) {
+  return a.emap ? launch_x_variant<NX, F, true>(a, s) : launch_x_variant<NX, F, false>(a, s);
 }
 
 cudaError_t run_xpass(int nx, int nf, const XPassArgs& a, cudaStream_t s) {

@@ -36,6 +36,11 @@ struct XPassArgs {
   float kh[3];         // kappa_f * dz/2, including the 1/2 SH factor for 2 fields
   float kh2[3];        // kh / 2 (exact)
   float scale;         // output scale for XM_INV
+  // transverse mismatch map: per-(x, y) stage phase factors [4][ny][nx]
+  // (B start, B quarter-step, A start, A quarter-step; see run_map_tables),
+  // or NULL for a mismatch uniform across the grid
+  const float2* emap;
+  int ny;
 };
 
 struct AxisArgs {
@@ -213,7 +218,7 @@ __host__ __device__ constexpr int xtile_smem_floats2(int nf) {
   return 6 * nf + nf * xtile_rows<NX, THREADS>() * XchRow::pitch(NX);
 }
 
-template <int NX, int F, int THREADS>
+template <int NX, int F, int THREADS, bool MAP = false>
 __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, const float2* coef, float2* rowbuf) {
   using PL = FftPlan<NX>;
   constexpr int E = PL::E;
@@ -264,6 +269,8 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
 
   // 2. the RK4 half steps, point by point over the owned positions
   if (mode == XM_NL_MID || mode == XM_NL_LAST || mode == XM_NL_FIRST) {
+    const long long nxy = (long long)p.ny * NX;
+    const float2* emap = MAP ? p.emap + (act ? row % p.ny : 0) * NX : nullptr;
 #pragma unroll 1
     for (int e = 0; e < E; ++e) {
       const int pos = t + (e / RF0) * T + (e % RF0) * SF0;
@@ -271,8 +278,28 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
       float2 a[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) a[f] = myrow[f * ROWS * PITCH + off];
-      if (mode != XM_NL_FIRST) rk4<F>(a, coef, p.kh, p.kh2);
-      if (mode != XM_NL_LAST) rk4<F>(a, coef + 3, p.kh, p.kh2);
+      if constexpr (MAP) {
+        // e^{i Phi(x, y, z_s)} = T V^s at this point, for the B and A stages
+        if (mode != XM_NL_FIRST) {
+          float2 e3[3];
+          const float2 v = __ldg(emap + nxy + pos);
+          e3[0] = __ldg(emap + pos);
+          e3[1] = cmul(e3[0], v);
+          e3[2] = cmul(e3[1], v);
+          rk4<F>(a, e3, p.kh, p.kh2);
+        }
+        if (mode != XM_NL_LAST) {
+          float2 e3[3];
+          const float2 v = __ldg(emap + 3 * nxy + pos);
+          e3[0] = __ldg(emap + 2 * nxy + pos);
+          e3[1] = cmul(e3[0], v);
+          e3[2] = cmul(e3[1], v);
+          rk4<F>(a, e3, p.kh, p.kh2);
+        }
+      } else {
+        if (mode != XM_NL_FIRST) rk4<F>(a, coef, p.kh, p.kh2);
+        if (mode != XM_NL_LAST) rk4<F>(a, coef + 3, p.kh, p.kh2);
+      }
 #pragma unroll
       for (int f = 0; f < F; ++f) myrow[f * ROWS * PITCH + off] = a[f];
     }
@@ -310,16 +337,17 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
   }
 }
 
-template <int NX, int F>
+// MAP: per-point stage phases from a transverse mismatch map (p.emap)
+template <int NX, int F, bool MAP>
 __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
     xpass_kernel(const XPassArgs p) {
   constexpr int THREADS = xpass_threads<NX>();
   extern __shared__ float4 sm4[];
   float2* coef = reinterpret_cast<float2*>(sm4);
   float2* rowbuf = coef + 6 * F;
-  nl_coefficients<F>(p, coef);
+  if constexpr (!MAP) nl_coefficients<F>(p, coef);
   __syncthreads();
-  xpass_tile<NX, F, THREADS>(p, blockIdx.x, coef, rowbuf);
+  xpass_tile<NX, F, THREADS, MAP>(p, blockIdx.x, coef, rowbuf);
 }
 
 // w (1 + d) for a propagator factor in delta form: the small product w d is
@@ -492,6 +520,19 @@ struct TableArgs {
   double k[3], rho[3], delta[3], k2[3], k3[3], alpha[3];
 };
 cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s);
+// Stage phase factors of one x-pass under a transverse mismatch map m(x, y):
+// Phi(x, y, z) = Phi(z) + m z.  With zj the distance of the B step's start
+// (phiB = Phi there, dkB its mismatch) and zA that of the A step's start,
+//   emap[0] = e^{i (phiB + dkB dz/2 + m (zj + dz/2))},  emap[1] = e^{i (dkB + m) dz/4},
+//   emap[2] = e^{i (phiA + m zA)},                        emap[3] = e^{i (dkA + m) dz/4},
+// each [ny][nx]; phases in FP64 reduced mod 2 pi before the FP32 sincos.
+struct MapArgs {
+  const double* dkmap;
+  float2* emap;
+  long long nxy;
+  double phiB, dkB, zB, phiA, dkA, zA, dz;
+};
+cudaError_t run_map_tables(const MapArgs& a, cudaStream_t s);
 // the linear step's multiply element by element (grids with nt = 1)
 cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s);
 // diagnostics (k_diag.cu): out[f nt + k] = sum_{x,y} |A_f(tau_k)|^2, and

@@ -412,3 +412,81 @@ def test_tma_tau_pass_is_bit_identical_to_plain(maker):
         s.close()
     for f in range(3):
         assert np.array_equal(outs[0][f], outs[2][f]) and np.array_equal(outs[1][f], outs[2][f])
+
+
+# ------------------------------------------------- transverse mismatch map
+def _map_case(nx, ny, nt, nf, seed):
+    g = wl.Grid(nx, ny, nt, 4 * wl.UM, 4 * wl.UM, 30 * wl.FS)
+    fields = _opg_fields(alpha=30.0, k3=4e-40)
+    if nf == 2:
+        fields = [wl.FieldParams(wl.LAM_SH, wl.N_SH, delta=5e-11, k2=1e-25, rho=1e-3, alpha=20.0),
+                  wl.FieldParams(wl.LAM_F, wl.N_F, k2=2e-25)]
+    rng = np.random.default_rng(seed)
+    init = [_smooth(g, rng, 5e7) for _ in range(nf)]
+    x, y, _ = g.axes()
+    fan = 4e6 * x[None, :] * np.ones((ny, 1))          # fan-out: 4000 1/m per mm of x
+    bump = 800.0 * np.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / (0.2 * nx * g.dx) ** 2)
+    return g, fields, init, fan + bump
+
+
+@pytest.mark.parametrize("shape,nf", [((48, 24, 96), 3), ((64, 32, 64), 2), ((64, 64, 1), 2)],
+                         ids=["48x24x96_f3", "64x32x64_f2", "64x64x1_f2"])
+def test_dk_map_matches_oracle(shape, nf):
+    br = _br()
+    g, fields, init, m = _map_case(*shape, nf, sum(shape) + nf)
+    prof = np.random.default_rng(9).normal(0.0, 300.0, 12)
+    nz, dz, dk = 16, 8 * wl.UM, 700.0
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map(m)
+    s.set_dk_profile(prof)
+    s.set_fields(_dev(init))
+    s.propagate(7, dz)
+    s.propagate(nz - 7, dz)  # resumes: z carries across calls
+    got = s.get_fields()
+    s.close()
+    dks = np.full(nz, dk)
+    dks[:12] = prof
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    ref, _ = oracle.propagate_map(prob, [_c64(a).astype(np.complex128) for a in init], nz, dz, dks, m)
+    errs = [rel_l2(got[f], ref[f]) for f in range(nf)]
+    record("dk_map_" + "x".join(map(str, shape)) + f"_f{nf}", field_rel_l2=errs)
+    for f in range(nf):
+        assert errs[f] < FIELD_TOL, (f, errs[f])
+
+
+def test_dk_map_zero_uniform_and_cleared():
+    """A zero map reproduces the map-free run to FP32 rounding, a uniform map
+    c the run with dk + c; clearing the map restores the map-free result bit
+    for bit; the adjoint refuses a map."""
+    br = _br()
+    g, fields, init, _ = _map_case(32, 16, 32, 3, 5)
+    dz, dk = 8 * wl.UM, 700.0
+
+    def run(m, dk_):
+        s = br.Solver(g, fields, wl.D_EFF, dk_)
+        if m is not None:
+            s.set_dk_map(m)
+        s.set_fields(_dev(init))
+        s.propagate(12, dz)
+        out = s.get_fields()
+        s.close()
+        return out
+
+    plain = run(None, dk)
+    zero = run(np.zeros((16, 32)), dk)
+    shifted = run(np.full((16, 32), 350.0), dk - 350.0)
+    for f in range(3):
+        assert rel_l2(zero[f], plain[f]) < 2e-6
+        assert rel_l2(shifted[f], plain[f]) < 1e-5
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map(np.zeros((16, 32)))
+    s.set_dk_map(None)
+    s.set_fields(_dev(init))
+    s.propagate(12, dz)
+    cleared = s.get_fields()
+    for f in range(3):
+        assert np.array_equal(cleared[f], plain[f])
+    s.set_dk_map(np.zeros((16, 32)))
+    with pytest.raises(br.BrahmsError):
+        s.adjoint_forward(_dev(init), np.zeros(4), 4, dz, np.ones(3))
+    s.close()
