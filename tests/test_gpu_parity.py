@@ -490,3 +490,23 @@ def test_dk_map_zero_uniform_and_cleared():
     with pytest.raises(br.BrahmsError):
         s.adjoint_forward(_dev(init), np.zeros(4), 4, dz, np.ones(3))
     s.close()
+
+
+EXTREME = [(4096, 2, 2), (2, 4096, 2), (2, 2, 4096), (768, 6, 4), (6, 768, 4), (4, 6, 768), (2, 2, 2)]
+
+
+@pytest.mark.parametrize("shape", EXTREME, ids=lambda s: "x".join(map(str, s)))
+def test_extreme_lengths_propagate_matches_oracle(shape):
+    """The longest and shortest supported lengths on each axis through the
+    whole split step (x-pass, y-passes, tau-propagator), all terms on."""
+    nx, ny, nt = shape
+    g = wl.Grid(nx, ny, nt, 2 * wl.UM, 2 * wl.UM, 10 * wl.FS)
+    fields = _opg_fields(alpha=30.0, k3=4e-40)
+    rng = np.random.default_rng(nx * 3 + ny * 5 + nt * 7)
+    init = [_smooth(g, rng, 5e7) for _ in range(3)]
+    got, ref, e_gpu, e_ref = _run_both(g, fields, init, 10, 4 * wl.UM, 700.0)
+    errs = [rel_l2(got[f], ref[f]) for f in range(3)]
+    record("extreme_" + "x".join(map(str, shape)), field_rel_l2=errs)
+    for f in range(3):
+        assert errs[f] < FIELD_TOL, (f, errs[f])
+        assert abs(e_gpu[f] / e_ref[f] - 1) < ENERGY_PARITY_TOL
