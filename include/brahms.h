@@ -145,13 +145,22 @@ brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
  * 4 other) are written to the first nkinds entries; this waits for the stream. */
 brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* launches, int nkinds);
 
-/* Implementation options.  BRAHMS_OPT_TMA_TAU: value 16 or 8 makes the
+/* Implementation options; every setting computes identical numbers.
+ * BRAHMS_OPT_FIELD_STREAMS: 1 runs each field's y-forward, tau-propagator
+ * and y-inverse of a step on a stream of its own (created by the library),
+ * each field's y-forward starting after the previous field's, so that
+ * DRAM-bound and compute-bound passes of different fields overlap; the
+ * x-pass, which couples the fields, waits for all of them on the context
+ * stream.  0 runs every pass on the context stream; 2 (the default) chooses
+ * 1 for grids of at most 2^23 points and 0 above.  Per-kernel timing with
+ * field streams measures kernels that may share the GPU.
+ * BRAHMS_OPT_TMA_TAU: value 16 or 8 makes the
  * tau-pass of brahms_propagate a persistent kernel that stages tiles of that
  * many x columns through shared memory with double-buffered TMA copies
  * (needs nt in {256, 512} and nx >= 16, else E_SIZE); 0 (the default) keeps
- * the plain tau-pass.  Both compute identical numbers.  E_ARG for an unknown
+ * the plain tau-pass (and turns the field streams off while set).  E_ARG for an unknown
  * option or value.  brahms_get_option returns the current value or -1. */
-enum { BRAHMS_OPT_TMA_TAU = 1 };
+enum { BRAHMS_OPT_TMA_TAU = 1, BRAHMS_OPT_FIELD_STREAMS = 2 };
 brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value);
 int brahms_get_option(const brahms_ctx* ctx, int option);
 

@@ -31,6 +31,7 @@ BRAHMS_C128 = 1
 
 KIND_NAMES = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
 BRAHMS_OPT_TMA_TAU = 1
+BRAHMS_OPT_FIELD_STREAMS = 2
 
 # Every entry point declared in include/brahms.h, with its ctypes signature.
 _c = ctypes

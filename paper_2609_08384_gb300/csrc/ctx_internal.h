@@ -80,6 +80,10 @@ struct brahms_ctx {
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns
+  // per-field streams for the y/tau/y chain of a step (created on first use)
+  int field_streams = 2;  // 0 off, 1 on, 2 on for grids of at most 2^23 points
+  cudaStream_t fstream[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_x = nullptr, ev_y[3] = {nullptr, nullptr, nullptr}, ev_done[3] = {nullptr, nullptr, nullptr};
   double tab_dz = NAN;
   bool have_fields = false;
   double z = 0.0, phi = 0.0;
@@ -144,22 +148,26 @@ inline cudaEvent_t take_event(brahms_ctx* c) {
 }
 
 // Launch wrapper: counts launches and, when timing is on, brackets the
-// launch with events on the context stream.
+// launch with events on the stream it is enqueued on.
 template <class Fn>
-inline cudaError_t launch(brahms_ctx* c, int kind, int nlaunch, Fn fn) {
+inline cudaError_t launch_on(brahms_ctx* c, cudaStream_t st, int kind, int nlaunch, Fn fn) {
   cudaEvent_t a = nullptr, b = nullptr;
   if (c->timing) {
     a = take_event(c);
     b = take_event(c);
-    if (a && b) cudaEventRecord(a, c->stream);
+    if (a && b) cudaEventRecord(a, st);
   }
   cudaError_t e = fn();
   c->launches += nlaunch;
   if (c->timing && a && b) {
-    cudaEventRecord(b, c->stream);
+    cudaEventRecord(b, st);
     c->timed.push_back({kind, a, b});
   }
   return e;
+}
+template <class Fn>
+inline cudaError_t launch(brahms_ctx* c, int kind, int nlaunch, Fn fn) {
+  return launch_on(c, c->stream, kind, nlaunch, fn);
 }
 
 inline brahms_status collect_timing(brahms_ctx* ctx) {

@@ -510,3 +510,31 @@ def test_extreme_lengths_propagate_matches_oracle(shape):
     for f in range(3):
         assert errs[f] < FIELD_TOL, (f, errs[f])
         assert abs(e_gpu[f] / e_ref[f] - 1) < ENERGY_PARITY_TOL
+
+
+@pytest.mark.parametrize("maker", ["opg", "sfg", "shg"])
+def test_field_streams_are_bit_identical(maker):
+    """Per-field streams for the y/tau/y chain compute exactly what the
+    single-stream sequence computes."""
+    br = _br()
+    if maker == "opg":
+        p = wl.problem_opg()
+        init = wl.inputs_opg(p)
+    elif maker == "sfg":
+        p = wl.problem_sfg()
+        init = wl.inputs_sfg(p)
+    else:
+        p = wl.problem_shg_small()
+        init = wl.inputs_shg_small(p)
+    outs = []
+    for split in (0, 1):
+        s = br.Solver(p.grid, p.fields, p.d_eff, 40.0)
+        s.set_option(br.BRAHMS_OPT_FIELD_STREAMS, split)
+        assert s.get_option(br.BRAHMS_OPT_FIELD_STREAMS) == split
+        s.set_fields(_dev(init))
+        s.propagate(4, p.dz)
+        s.propagate(3, p.dz)
+        outs.append(s.get_fields())
+        s.close()
+    for f in range(p.nfields):
+        assert np.array_equal(outs[0][f], outs[1][f])
