@@ -82,13 +82,16 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+# the sources that define the four pass kernels whose DRAM traffic is recorded
+KERNEL_SOURCES = ("fft_core.cuh", "kernels.cuh", "k_xpass.cu", "k_axis.cu")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2609_08384_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode() + f.read())
+    for fn in KERNEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
     return h.hexdigest()[:16]
 
 
