@@ -4,12 +4,13 @@
 //
 // Forward: the state is checkpointed every K steps (K = ceil(sqrt(nz)) by
 // default) while the fused propagation runs.  Backward: segments are visited
-// last to first; each is recomputed from its checkpoint one step at a time
-// (keeping the K step states), then reversed step by step:
-//   a2 = L(N_A(A_j))                (recomputed)
-//   G <- N_B^T(a2) G                (RK4 reverse mode, stage phase sensitivities)
-//   G <- IDFT3( conj(P) DFT3(G) )   (adjoint of the linear step)
-//   G <- N_A^T(A_j) G
+// last to first.  Each is recomputed from its checkpoint with the recording
+// x-pass, which keeps the states entering every B half step (a2_j) and every
+// A half step (A_j).  The adjoint then runs the forward's pass structure in
+// reverse: at each boundary b between steps b-1 and b one reverse x-pass
+// (inverse x-FFT, reverse of N_A at A_b, reverse of N_B at a2_{b-1}, forward
+// x-FFT), then the adjoint of the linear step, IDFT3(conj(P) DFT3), as the
+// y-forward, conjugated tau-propagator and y-inverse passes.
 // The mismatch gradient follows from the stage sensitivities dJ/dPhi with
 // Phi(z) = Phi_j + dk_j (z - z_j); the phase gradient from the tau-spectra of
 // the adjoint and of the phased input.
@@ -21,8 +22,6 @@ using namespace brahms_host;
 
 namespace {
 
-constexpr int kVjpBlocks = 152 * 4;
-
 brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
   const size_t state = sizeof(float2) * (size_t)ctx->nf * (size_t)ctx->npoints();
   size_t off = 0;
@@ -31,10 +30,13 @@ brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
     off += align256(b);
     return o;
   };
-  const size_t o_ck = take(state * nseg), o_seg = take(state * K), o_w = take(state), o_g = take(state);
+  // checkpoints; per segment the recorded states entering each step's B half
+  // (K) and A half (K); the recomputation's state; the adjoint
+  const size_t o_ck = take(state * nseg), o_seg = take(state * 2 * K), o_w = take(state), o_g = take(state);
   const size_t o_tab = take(sizeof(float2) * (ctx->nx + ctx->ny + ctx->nt));
   const size_t o_phi = take(sizeof(double) * ctx->nt), o_acc = take(sizeof(double) * ctx->nt);
-  const size_t o_part = take(sizeof(double) * (size_t)nz * 2 * kVjpBlocks * 3);
+  const long long ncta = brahms::xpass_adjoint_ctas(ctx->nx, (long long)ctx->ny * ctx->nt);
+  const size_t o_part = take(sizeof(double) * (size_t)(ncta > 0 ? ncta : 1) * 6);
   const size_t o_sens = take(sizeof(double) * (size_t)nz * 6);
   if (off > ctx->adj_bytes) {
     if (ctx->adj_mem) cudaFree(ctx->adj_mem);
@@ -56,27 +58,6 @@ brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
   ctx->adj_acc = (double*)(m + o_acc);
   ctx->adj_part = (double*)(m + o_part);
   ctx->adj_sens = (double*)(m + o_sens);
-  return BRAHMS_OK;
-}
-
-// One linear step (forward or adjoint) on `data`, real space in and out.
-brahms_status linear_on(brahms_ctx* ctx, float2* data, double dz, bool adjoint) {
-  const int nx = ctx->nx, ny = ctx->ny, nt = ctx->nt, nf = ctx->nf;
-  brahms::XPassArgs xf = xargs(ctx, brahms::XM_FWD, dz), xi = xargs(ctx, brahms::XM_INV, dz);
-  xf.data = data;
-  xi.data = data;
-  xi.scale = 1.f;  // 1/(nx ny nt) is part of the tau-pass multiplier
-  brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
-  ay.data = data;
-  at.data = data;
-  at.conj_p = adjoint ? 1 : 0;
-  brahms_status s = build_tables(ctx, dz);
-  if (s != BRAHMS_OK) return s;
-  BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xf, ctx->stream); }));
-  BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
-  BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
-  BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ay, ctx->stream); }));
-  BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xi, ctx->stream); }));
   return BRAHMS_OK;
 }
 
@@ -170,61 +151,99 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
   for (int f = 0; f < nf; ++f) sc[f] = (float)(2.0 * ctx->adj_weights[f] * gscale);
   BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_scale_fields(ctx->state, ctx->adj_g, n, nf, n, sc, ctx->stream); }));
   const brahms::XPassArgs base = xargs(ctx, brahms::XM_NL_FIRST, dz);
+  const brahms::AxisArgs ay0 = aargs(ctx, 1), at0 = aargs(ctx, 2);
+  brahms_status st = build_tables(ctx, dz);
+  if (st != BRAHMS_OK) return st;
+  auto dk_at = [&](int j) { return j < nz ? ctx->adj_dk[j] : ctx->dk; };
+  // the segment's recorded states: B[j - j0] enters step j's B half step
+  // (a2_j), A[j - j0] enters step j's A half step (A_j, j > j0)
+  float2* recB = ctx->adj_seg;
+  float2* recA = ctx->adj_seg + (size_t)K * nf * n;
+  // y-forward, tau-propagator (conjugated in reverse) and y-inverse on data
+  auto yty = [&](float2* data, bool adjoint) -> brahms_status {
+    brahms::AxisArgs ay = ay0, at = at0;
+    ay.data = data;
+    at.data = data;
+    at.conj_p = adjoint ? 1 : 0;
+    BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
+    BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
+    BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));
+    return BRAHMS_OK;
+  };
+  // reverse x-pass at boundary b (xa: A_b or NULL, xb: a2_{b-1} or NULL)
+  auto reverse_x = [&](int b, const float2* xa, const float2* xb) -> brahms_status {
+    brahms::XAdjArgs r{};
+    r.g = ctx->adj_g;
+    r.xa = xa;
+    r.xb = xb;
+    r.fstride = n;
+    r.rows = (long long)ctx->ny * ctx->nt;
+    r.tw = ctx->twx;
+    r.from_k = b < nz ? 1 : 0;
+    r.to_k = b > 0 ? 1 : 0;
+    r.h = 0.5 * dz;
+    for (int f = 0; f < nf; ++f) r.kh[f] = base.kh[f];
+    if (xa) {
+      r.phiA = ctx->adj_phis[b];
+      r.dkA = dk_at(b);
+    }
+    if (xb) {
+      r.dkB = dk_at(b - 1);
+      r.phiB = ctx->adj_phis[b - 1] + r.dkB * 0.5 * dz;
+    }
+    r.partial = ctx->adj_part;
+    long long ncta = 0;
+    BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_adjoint(nx, nf, r, &ncta, ctx->stream); }));
+    double* sA = xa ? ctx->adj_sens + (size_t)b * 6 : nullptr;
+    double* sB = xb ? ctx->adj_sens + (size_t)(b - 1) * 6 + 3 : nullptr;
+    BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_sens_boundary(ctx->adj_part, ncta, sA, sB, ctx->stream); }));
+    return BRAHMS_OK;
+  };
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int j0 = seg * K, j1 = std::min(nz, j0 + K);
-    // recompute the segment's step states A_j0 .. A_{j1-1}
-    BR_CK(cudaMemcpyAsync(ctx->state, ctx->adj_ckpt + (size_t)seg * nf * n, sbytes, cudaMemcpyDeviceToDevice,
+    // recompute the segment from its checkpoint, recording a2_j and A_j
+    BR_CK(cudaMemcpyAsync(ctx->adj_work, ctx->adj_ckpt + (size_t)seg * nf * n, sbytes, cudaMemcpyDeviceToDevice,
                           ctx->stream));
-    for (int j = j0; j < j1; ++j) {
-      BR_CK(cudaMemcpyAsync(ctx->adj_seg + (size_t)(j - j0) * nf * n, ctx->state, sbytes, cudaMemcpyDeviceToDevice,
-                            ctx->stream));
-      if (j < j1 - 1) {
-        ctx->step = j;
-        ctx->phi = ctx->adj_phis[j];
-        brahms_status s = brahms_propagate(ctx, 1, dz);
-        if (s != BRAHMS_OK) return s;
-      }
+    {
+      brahms::XPassArgs x = base;
+      x.data = ctx->adj_work;
+      x.phiA = ctx->adj_phis[j0];
+      x.dkA = dk_at(j0);
+      BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, x, ctx->stream); }));
     }
-    for (int j = j1 - 1; j >= j0; --j) {
-      float2* aj = ctx->adj_seg + (size_t)(j - j0) * nf * n;
-      const double dkj = ctx->adj_dk[j], phj = ctx->adj_phis[j];
-      // a2 = L(N_A(A_j)) in the work buffer
-      BR_CK(cudaMemcpyAsync(ctx->adj_work, aj, sbytes, cudaMemcpyDeviceToDevice, ctx->stream));
-      {
-        brahms::XPassArgs xa = base;
-        xa.data = ctx->adj_work;
-        xa.phiA = phj;
-        xa.dkA = dkj;
-        BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xa, ctx->stream); }));
-        brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
-        ay.data = ctx->adj_work;
-        at.data = ctx->adj_work;
-        brahms_status s = build_tables(ctx, dz);
-        if (s != BRAHMS_OK) return s;
-        BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
-        BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
-        BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));
-        brahms::XPassArgs xi = xargs(ctx, brahms::XM_INV, dz);
-        xi.data = ctx->adj_work;
-        xi.scale = 1.f;
-        BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, xi, ctx->stream); }));
-      }
-      double* partB = ctx->adj_part + ((size_t)j * 2 + 1) * kVjpBlocks * 3;
-      double* partA = ctx->adj_part + ((size_t)j * 2) * kVjpBlocks * 3;
-      BR_CK(launch(ctx, 4, 1, [&] {
-        return brahms::run_rk4_vjp(nf, ctx->adj_work, ctx->adj_g, n, n, phj + dkj * 0.5 * dz, dkj, 0.5 * dz, base.kh,
-                                   partB, kVjpBlocks, ctx->stream);
-      }));
-      brahms_status s = linear_on(ctx, ctx->adj_g, dz, true);
-      if (s != BRAHMS_OK) return s;
-      BR_CK(launch(ctx, 4, 1, [&] {
-        return brahms::run_rk4_vjp(nf, aj, ctx->adj_g, n, n, phj, dkj, 0.5 * dz, base.kh, partA, kVjpBlocks,
-                                   ctx->stream);
-      }));
+    for (int j = j0; j < j1; ++j) {
+      brahms_status s2 = yty(ctx->adj_work, false);
+      if (s2 != BRAHMS_OK) return s2;
+      const bool last = j == j1 - 1;
+      brahms::XPassArgs x = xargs(ctx, last ? brahms::XM_NL_LAST : brahms::XM_NL_MID, dz);
+      x.data = ctx->adj_work;
+      x.phiB = ctx->adj_phis[j];
+      x.dkB = dk_at(j);
+      x.phiA = ctx->adj_phis[j + 1];
+      x.dkA = dk_at(j + 1);
+      x.rec_b = recB + (size_t)(j - j0) * nf * n;
+      x.rec_a = last ? nullptr : recA + (size_t)(j + 1 - j0) * nf * n;
+      BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_record(nx, nf, x, ctx->stream); }));
+    }
+    // reverse through boundaries j1 .. j0 + 1, each followed by the linear
+    // adjoint of the step before it
+    for (int b = j1; b > j0; --b) {
+      const float2* xa = b == nz ? nullptr
+                                 : (b == j1 ? ctx->adj_ckpt + (size_t)(seg + 1) * nf * n
+                                            : recA + (size_t)(b - j0) * nf * n);
+      const float2* xb = recB + (size_t)(b - 1 - j0) * nf * n;
+      brahms_status s2 = reverse_x(b, xa, xb);
+      if (s2 != BRAHMS_OK) return s2;
+      s2 = yty(ctx->adj_g, true);
+      if (s2 != BRAHMS_OK) return s2;
     }
   }
+  // boundary 0: the reverse of step 0's A half step, back to real space
+  {
+    brahms_status s2 = reverse_x(0, ctx->adj_ckpt, nullptr);
+    if (s2 != BRAHMS_OK) return s2;
+  }
   // mismatch gradient from the stage sensitivities
-  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_sens_reduce(ctx->adj_part, kVjpBlocks, nz, ctx->adj_sens, ctx->stream); }));
   std::vector<double> S((size_t)nz * 6);
   BR_CK(cudaMemcpyAsync(S.data(), ctx->adj_sens, sizeof(double) * S.size(), cudaMemcpyDeviceToHost, ctx->stream));
   std::vector<double> acc;

@@ -101,11 +101,11 @@ struct brahms_ctx {
   char* adj_mem = nullptr;
   size_t adj_bytes = 0;
   float2* adj_ckpt = nullptr;  // checkpoints, one state each
-  float2* adj_seg = nullptr;   // states of one segment
+  float2* adj_seg = nullptr;   // recorded states of one segment: B half-step inputs [K], A half-step inputs [K]
   float2* adj_work = nullptr;  // recomputed state within a step
   float2* adj_g = nullptr;     // adjoint state
   float2* adj_tab = nullptr;   // spectral-phase tables: x (nx), y (ny), tau (nt)
-  double* adj_part = nullptr;  // stage-sensitivity partials
+  double* adj_part = nullptr;  // stage-sensitivity partials of one reverse x-pass [CTAs][6]
   double* adj_sens = nullptr;  // [nz][6] stage sensitivities
   double* adj_phi_dev = nullptr;  // spectral phase (nt)
   double* adj_acc = nullptr;      // phase-gradient accumulators (nt)

@@ -41,6 +41,10 @@ struct XPassArgs {
   // or NULL for a mismatch uniform across the grid
   const float2* emap;
   int ny;
+  // recording (adjoint recomputation): real-space copies of the state that
+  // enters the B half step and of the state that enters the A half step, or NULL
+  float2* rec_b;
+  float2* rec_a;
 };
 
 struct AxisArgs {
@@ -218,7 +222,7 @@ __host__ __device__ constexpr int xtile_smem_floats2(int nf) {
   return 6 * nf + nf * xtile_rows<NX, THREADS>() * XchRow::pitch(NX);
 }
 
-template <int NX, int F, int THREADS, bool MAP = false>
+template <int NX, int F, int THREADS, bool MAP = false, bool REC = false>
 __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, const float2* coef, float2* rowbuf) {
   using PL = FftPlan<NX>;
   constexpr int E = PL::E;
@@ -297,8 +301,24 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
           rk4<F>(a, e3, p.kh, p.kh2);
         }
       } else {
-        if (mode != XM_NL_FIRST) rk4<F>(a, coef, p.kh, p.kh2);
-        if (mode != XM_NL_LAST) rk4<F>(a, coef + 3, p.kh, p.kh2);
+        if (mode != XM_NL_FIRST) {
+          if constexpr (REC) {
+            if (p.rec_b && act) {
+#pragma unroll
+              for (int f = 0; f < F; ++f) p.rec_b[f * p.fstride + row * NX + pos] = a[f];
+            }
+          }
+          rk4<F>(a, coef, p.kh, p.kh2);
+        }
+        if (mode != XM_NL_LAST) {
+          if constexpr (REC) {
+            if (p.rec_a && act) {
+#pragma unroll
+              for (int f = 0; f < F; ++f) p.rec_a[f * p.fstride + row * NX + pos] = a[f];
+            }
+          }
+          rk4<F>(a, coef + 3, p.kh, p.kh2);
+        }
       }
 #pragma unroll
       for (int f = 0; f < F; ++f) myrow[f * ROWS * PITCH + off] = a[f];
@@ -337,8 +357,9 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
   }
 }
 
-// MAP: per-point stage phases from a transverse mismatch map (p.emap)
-template <int NX, int F, bool MAP>
+// MAP: per-point stage phases from a transverse mismatch map (p.emap);
+// REC: record the half steps' input states (p.rec_b, p.rec_a)
+template <int NX, int F, bool MAP, bool REC = false>
 __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
     xpass_kernel(const XPassArgs p) {
   constexpr int THREADS = xpass_threads<NX>();
@@ -347,7 +368,7 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
   float2* rowbuf = coef + 6 * F;
   if constexpr (!MAP) nl_coefficients<F>(p, coef);
   __syncthreads();
-  xpass_tile<NX, F, THREADS, MAP>(p, blockIdx.x, coef, rowbuf);
+  xpass_tile<NX, F, THREADS, MAP, REC>(p, blockIdx.x, coef, rowbuf);
 }
 
 // w (1 + d) for a propagator factor in delta form: the small product w d is
@@ -546,13 +567,35 @@ cudaError_t run_energy(const float2* data, long long n, int nf, long long fstrid
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
 cudaError_t run_c64_to_c128(const float2* in, double2* out, long long n, cudaStream_t s);
 
+// adjoint recomputation and reverse x-pass (k_xadj.cu)
+// x-pass that also records the states entering its half steps (a.rec_b, a.rec_a)
+cudaError_t run_xpass_record(int nx, int nf, const XPassArgs& a, cudaStream_t s);
+// Reverse of one x-pass boundary: the adjoint g, in (kx, y, tau) when
+// from_k (else real space), goes through the inverse x-FFT, the reverse of
+// the A half step at state xa (if xa), the reverse of the B half step at
+// state xb (if xb), and the forward x-FFT when to_k.  Each CTA writes its
+// six stage-phase sensitivity sums (A: start, middle, end; B: the same) to
+// partial[blockIdx.x][6]; *ncta receives the CTA count.
+struct XAdjArgs {
+  float2* g;
+  const float2* xa;
+  const float2* xb;
+  long long fstride, rows;
+  const float4* tw;
+  int from_k, to_k;
+  double phiA, dkA, phiB, dkB, h;  // phase and mismatch at the start of each half step; h = dz/2
+  float kh[3];                     // kappa_f h (1/2 on the SH equation for two fields)
+  double* partial;
+};
+cudaError_t run_xpass_adjoint(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s);
+// sensA[k] = sum_c partial[c][k], sensB[k] = sum_c partial[c][3 + k] (either may be NULL)
+cudaError_t run_sens_boundary(const double* partial, long long ncta, double* sensA, double* sensB, cudaStream_t s);
+long long xpass_adjoint_ctas(int nx, long long rows);
+
 // adjoint kernels (k_adjoint.cu)
-cudaError_t run_rk4_vjp(int nf, const float2* x, float2* g, long long n, long long fstride, double phi_a, double dk,
-                        double h, const float* kh, double* partial, int nblocks, cudaStream_t s);
 cudaError_t run_scale_fields(const float2* a, float2* g, long long n, int nf, long long fstride, const float* s,
                              cudaStream_t st);
 cudaError_t run_phase_grad(const float2* gh, const float2* ah, long long plane, int nt, double* acc, cudaStream_t s);
-cudaError_t run_sens_reduce(const double* partial, int nblocks, int nz, double* sens, cudaStream_t s);
 cudaError_t run_phase_tables(float2* px, int nx, float2* py, int ny, float2* pt, int nt, const double* phi, int sign,
                              cudaStream_t s);
 
