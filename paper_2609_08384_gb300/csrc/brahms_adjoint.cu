@@ -160,11 +160,13 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
   float2* recB = ctx->adj_seg;
   float2* recA = ctx->adj_seg + (size_t)K * nf * n;
   // y-forward, tau-propagator (conjugated in reverse) and y-inverse on data
+  const bool split = use_field_streams(ctx);
   auto yty = [&](float2* data, bool adjoint) -> brahms_status {
     brahms::AxisArgs ay = ay0, at = at0;
     ay.data = data;
     at.data = data;
     at.conj_p = adjoint ? 1 : 0;
+    if (split) return enqueue_linear_split(ctx, ay, at);
     BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
     BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
     BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));

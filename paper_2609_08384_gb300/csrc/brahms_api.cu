@@ -187,33 +187,6 @@ brahms_status brahms_set_dk_profile(brahms_ctx* ctx, const double* dk, int n) {
   return BRAHMS_OK;
 }
 
-namespace {
-
-// streams and events of the per-field chains, created on first use
-brahms_status field_streams_ready(brahms_ctx* ctx) {
-  if (ctx->ev_x) return BRAHMS_OK;
-  for (int f = 0; f < 3; ++f) {
-    BR_CK(cudaStreamCreateWithFlags(&ctx->fstream[f], cudaStreamNonBlocking));
-    BR_CK(cudaEventCreateWithFlags(&ctx->ev_y[f], cudaEventDisableTiming));
-    BR_CK(cudaEventCreateWithFlags(&ctx->ev_done[f], cudaEventDisableTiming));
-  }
-  BR_CK(cudaEventCreateWithFlags(&ctx->ev_x, cudaEventDisableTiming));
-  return BRAHMS_OK;
-}
-
-// strided-pencil arguments restricted to field f
-brahms::AxisArgs field_args(const brahms_ctx* ctx, const brahms::AxisArgs& a, int f) {
-  brahms::AxisArgs b = a;
-  b.data = a.data + (long long)f * a.fstride;
-  b.px = a.px + (long long)f * ctx->nx;
-  b.py = a.py + (long long)f * ctx->ny;
-  b.pt = a.pt + (long long)f * ctx->nt;
-  b.ntiles = a.ntiles / ctx->nf;
-  return b;
-}
-
-}  // namespace
-
 brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   if (!ctx) return BRAHMS_E_ARG;
   if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "propagate before set_fields");
@@ -237,35 +210,12 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   }
   // measured on GB300: 4.5 % faster on 128x128x256 (three fields), 1.6 %
   // slower on 256x256x512, where each field's passes already fill the GPU
-  const bool split = (ctx->field_streams == 1 || (ctx->field_streams == 2 && ctx->npoints() <= (1LL << 23))) &&
-                     ny > 1 && nt > 1 && !ctx->use_tma;
-  brahms::AxisArgs ayf[3], atf[3];
-  if (split) {
-    s = field_streams_ready(ctx);
-    if (s != BRAHMS_OK) return s;
-    for (int f = 0; f < nf; ++f) {
-      ayf[f] = field_args(ctx, ay, f);
-      atf[f] = field_args(ctx, at, f);
-    }
-  }
+  const bool split = use_field_streams(ctx);
   for (int i = 0; i < nz; ++i, ++j) {
     const double dkj = dk_of_step(ctx, j);
     if (split) {
-      // field f's y-forward, tau-propagator and y-inverse on stream f, field
-      // f+1 starting its y-forward once field f's is done, so that one
-      // field's DRAM-bound y-passes overlap another's tau-pass
-      BR_CK(cudaEventRecord(ctx->ev_x, ctx->stream));
-      for (int f = 0; f < nf; ++f) {
-        cudaStream_t st = ctx->fstream[f];
-        BR_CK(cudaStreamWaitEvent(st, ctx->ev_x, 0));
-        if (f > 0) BR_CK(cudaStreamWaitEvent(st, ctx->ev_y[f - 1], 0));
-        BR_CK(launch_on(ctx, st, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ayf[f], st); }));
-        BR_CK(cudaEventRecord(ctx->ev_y[f], st));
-        BR_CK(launch_on(ctx, st, 2, 1, [&] { return brahms::run_tpass_prop(nt, atf[f], st); }));
-        BR_CK(launch_on(ctx, st, 3, 1, [&] { return brahms::run_axis_fft(ny, 1, true, ayf[f], st); }));
-        BR_CK(cudaEventRecord(ctx->ev_done[f], st));
-      }
-      for (int f = 0; f < nf; ++f) BR_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_done[f], 0));
+      s = enqueue_linear_split(ctx, ay, at);
+      if (s != BRAHMS_OK) return s;
     } else {
       if (ny > 1) BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ny, 1, false, ay, ctx->stream); }));
       if (nt == 1)

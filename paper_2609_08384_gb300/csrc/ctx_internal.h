@@ -285,6 +285,61 @@ inline brahms::AxisArgs aargs(brahms_ctx* c, int axis, bool tau_prop = true) {
   return a;
 }
 
+// Per-field streams for the y-forward, tau-propagator and y-inverse of a
+// step: on for grids of at most 2^23 points unless set otherwise (measured on
+// GB300: 4.5 % faster on 128x128x256 with three fields, 1.6 % slower on
+// 256x256x512, where each field's passes already fill the GPU).
+inline bool use_field_streams(const brahms_ctx* c) {
+  return (c->field_streams == 1 || (c->field_streams == 2 && c->npoints() <= (1LL << 23))) && c->ny > 1 &&
+         c->nt > 1 && !c->use_tma;
+}
+
+// streams and events of the per-field chains, created on first use
+inline brahms_status field_streams_ready(brahms_ctx* ctx) {
+  if (ctx->ev_x) return BRAHMS_OK;
+  for (int f = 0; f < 3; ++f) {
+    BR_CK(cudaStreamCreateWithFlags(&ctx->fstream[f], cudaStreamNonBlocking));
+    BR_CK(cudaEventCreateWithFlags(&ctx->ev_y[f], cudaEventDisableTiming));
+    BR_CK(cudaEventCreateWithFlags(&ctx->ev_done[f], cudaEventDisableTiming));
+  }
+  BR_CK(cudaEventCreateWithFlags(&ctx->ev_x, cudaEventDisableTiming));
+  return BRAHMS_OK;
+}
+
+// strided-pencil arguments restricted to field f
+inline brahms::AxisArgs field_args(const brahms_ctx* ctx, const brahms::AxisArgs& a, int f) {
+  brahms::AxisArgs b = a;
+  b.data = a.data + (long long)f * a.fstride;
+  b.px = a.px + (long long)f * ctx->nx;
+  b.py = a.py + (long long)f * ctx->ny;
+  b.pt = a.pt + (long long)f * ctx->nt;
+  b.ntiles = a.ntiles / ctx->nf;
+  return b;
+}
+
+// The y-forward, tau-propagator and y-inverse of one step with field f's on
+// stream f, field f+1 starting its y-forward once field f's is done, so that
+// one field's DRAM-bound y-passes overlap another's tau-pass; the context
+// stream waits for all of them.
+inline brahms_status enqueue_linear_split(brahms_ctx* ctx, const brahms::AxisArgs& ay, const brahms::AxisArgs& at) {
+  brahms_status s = field_streams_ready(ctx);
+  if (s != BRAHMS_OK) return s;
+  BR_CK(cudaEventRecord(ctx->ev_x, ctx->stream));
+  for (int f = 0; f < ctx->nf; ++f) {
+    cudaStream_t st = ctx->fstream[f];
+    const brahms::AxisArgs ayf = field_args(ctx, ay, f), atf = field_args(ctx, at, f);
+    BR_CK(cudaStreamWaitEvent(st, ctx->ev_x, 0));
+    if (f > 0) BR_CK(cudaStreamWaitEvent(st, ctx->ev_y[f - 1], 0));
+    BR_CK(launch_on(ctx, st, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ayf, st); }));
+    BR_CK(cudaEventRecord(ctx->ev_y[f], st));
+    BR_CK(launch_on(ctx, st, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, atf, st); }));
+    BR_CK(launch_on(ctx, st, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ayf, st); }));
+    BR_CK(cudaEventRecord(ctx->ev_done[f], st));
+  }
+  for (int f = 0; f < ctx->nf; ++f) BR_CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_done[f], 0));
+  return BRAHMS_OK;
+}
+
 inline double dk_of_step(const brahms_ctx* c, long long j) {
   return j < (long long)c->dk_profile.size() ? c->dk_profile[(size_t)j] : c->dk;
 }
