@@ -402,7 +402,7 @@ brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value) {
     return BRAHMS_OK;
   }
   if (option == BRAHMS_OPT_FIELD_STREAMS) {
-    if (value < 0 || value > 2) return fail(ctx, BRAHMS_E_ARG, "field streams: 0, 1 or 2");
+    if (value != 0 && value != 1) return fail(ctx, BRAHMS_E_ARG, "field streams: 0 or 1");
     ctx->field_streams = value;
     return BRAHMS_OK;
   }

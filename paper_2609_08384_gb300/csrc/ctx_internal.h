@@ -81,7 +81,7 @@ struct brahms_ctx {
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns
   // per-field streams for the y/tau/y chain of a step (created on first use)
-  int field_streams = 2;  // 0 off, 1 on, 2 on for grids of at most 2^23 points
+  int field_streams = 0;  // 0 off (default), 1 on
   cudaStream_t fstream[3] = {nullptr, nullptr, nullptr};
   cudaEvent_t ev_x = nullptr, ev_y[3] = {nullptr, nullptr, nullptr}, ev_done[3] = {nullptr, nullptr, nullptr};
   double tab_dz = NAN;
@@ -286,12 +286,11 @@ inline brahms::AxisArgs aargs(brahms_ctx* c, int axis, bool tau_prop = true) {
 }
 
 // Per-field streams for the y-forward, tau-propagator and y-inverse of a
-// step: on for grids of at most 2^23 points unless set otherwise (measured on
-// GB300: 4.5 % faster on 128x128x256 with three fields, 1.6 % slower on
-// 256x256x512, where each field's passes already fill the GPU).
+// step, when the option asks for them (measured on GB300: 5 % faster on
+// 128x128x256 with three fields, 2-28 % slower on two-field and small grids,
+// within 3 % either way on larger ones).
 inline bool use_field_streams(const brahms_ctx* c) {
-  return (c->field_streams == 1 || (c->field_streams == 2 && c->npoints() <= (1LL << 23))) && c->ny > 1 &&
-         c->nt > 1 && !c->use_tma;
+  return c->field_streams == 1 && c->ny > 1 && c->nt > 1 && !c->use_tma;
 }
 
 // streams and events of the per-field chains, created on first use

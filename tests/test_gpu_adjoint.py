@@ -151,3 +151,20 @@ def test_autograd_function():
     (3.0 * Eta.apply(tphi, tdk, s, dev, nz, dz, w, 0)).backward()
     assert rel_l2(tphi.grad.numpy(), 3.0 * gphi) < 1e-4 and rel_l2(tdk.grad.numpy(), 3.0 * gdk) < 1e-4
     s.close()
+
+
+def test_field_streams_do_not_change_the_gradient():
+    """The adjoint's linear passes on per-field streams give the same bits."""
+    import paper_2609_08384_gb300 as br
+    nz, dz = 20, 20 * wl.UM
+    g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 61)
+    w = np.array([1e-20, 3e-21])
+    out = []
+    for split in (0, 1):
+        s = br.Solver(g, f, wl.D_EFF, 0.0)
+        s.set_option(br.BRAHMS_OPT_FIELD_STREAMS, split)
+        J = s.adjoint_forward([torch.from_numpy(a).cuda() for a in ins], dk, nz, dz, w, phi=phi, checkpoint_interval=6)
+        out.append((J,) + tuple(s.adjoint_backward(1.0)))
+        s.close()
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
