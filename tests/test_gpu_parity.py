@@ -538,3 +538,30 @@ def test_field_streams_are_bit_identical(maker):
         s.close()
     for f in range(p.nfields):
         assert np.array_equal(outs[0][f], outs[1][f])
+
+
+def test_status_codes_of_the_added_entry_points():
+    br = _br()
+    g = wl.Grid(32, 16, 64, 5 * wl.UM, 5 * wl.UM, 30 * wl.FS)
+    s = br.Solver(g, wl.shg_fields(), wl.D_EFF, 0.0)
+    with pytest.raises(br.BrahmsError) as ei:
+        s.diagnostics()  # no fields yet
+    assert ei.value.status == br.BRAHMS_E_STATE
+    m = np.zeros((16, 32))
+    m[3, 7] = np.inf
+    with pytest.raises(br.BrahmsError) as ei:
+        s.set_dk_map(m)
+    assert ei.value.status == br.BRAHMS_E_ARG
+    for opt, bad in ((br.BRAHMS_OPT_FIELD_STREAMS, 2), (br.BRAHMS_OPT_TMA_TAU, 5), (99, 0)):
+        with pytest.raises(br.BrahmsError) as ei:
+            s.set_option(opt, bad)
+        assert ei.value.status == br.BRAHMS_E_ARG
+    assert s.get_option(99) == -1
+    s.close()
+    # the adjoint needs a tau and a y extent
+    c = br.Solver(wl.Grid(32, 32, 1, 5 * wl.UM, 5 * wl.UM, 1 * wl.FS), wl.shg_fields(), wl.D_EFF, 0.0)
+    z = torch.zeros(1, 32, 32, dtype=torch.complex64).cuda()
+    with pytest.raises(br.BrahmsError) as ei:
+        c.adjoint_forward([z, z], np.zeros(3), 3, 1e-6, np.ones(2))
+    assert ei.value.status == br.BRAHMS_E_SIZE
+    c.close()
