@@ -17,7 +17,7 @@ constexpr double kC0 = 299792458.0;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kHbar = 1.054571817e-34;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int kRedBlocks = 152 * 4;  // energy partials per field
+constexpr int kRedBlocks = 152 * 2;  // energy partials per field (all fields' blocks in one wave)
 constexpr int kKinds = 5;
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }

@@ -13,15 +13,22 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// sum_{x,y} |A_f(x, y, tau_k)|^2 in FP64 for every (k, f): one CTA per plane
+// sum_{x,y} |A_f(x, y, tau_k)|^2 for every (k, f): one CTA per plane; two
+// points per 16-byte load, their squares summed in FP32 and accumulated in
+// FP64 (planes hold an even number of points)
 __global__ void __launch_bounds__(256) power_trace_kernel(const float2* __restrict__ data, long long plane,
                                                           int nt, long long fstride, double* out) {
   const int k = blockIdx.x, f = blockIdx.y;
   const float2* a = data + (long long)f * fstride + (long long)k * plane;
   double s = 0.0;
-  for (long long i = threadIdx.x; i < plane; i += blockDim.x) {
-    const float2 v = __ldcg(a + i);
-    s = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, s));
+  const float4* a4 = reinterpret_cast<const float4*>(a);
+  for (long long i = threadIdx.x; i < plane / 2; i += blockDim.x) {
+    const float4 v = __ldcg(a4 + i);
+    s += (double)fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, v.w * v.w)));
+  }
+  if ((plane & 1) && threadIdx.x == 0) {
+    const float2 v = __ldcg(a + plane - 1);
+    s += (double)fmaf(v.x, v.x, v.y * v.y);
   }
   __shared__ double red[8];
   s = warp_sum_d(s);

@@ -1,9 +1,9 @@
 """GPU diagnostics (temporal power trace, energy spectrum over Omega) against
 the oracle's, through the C ABI.
 
-On the same complex64 fields the power traces are both FP64 sums of the
-same squares (agreement to rounding order, 1e-12); the spectrum's tau
-transform is FP32 on the GPU (1e-5 of the peak bin).  After a propagation
+On the same complex64 fields the power traces agree to the GPU's FP32
+squares of point pairs (summed in FP64; 1e-7 of the peak); the spectrum's
+tau transform is FP32 on the GPU (1e-5 of the peak bin).  After a propagation
 the fields themselves differ by the propagation's FP32 error (2e-4)."""
 import numpy as np
 import pytest
@@ -69,7 +69,7 @@ def test_diagnostics_match_oracle_on_same_fields(shape):
     s_ref = oracle.spectrum(prob, a128)
     for f in range(nf):
         assert np.array_equal(again[f], arrs[f])  # the state is untouched
-        assert np.max(np.abs(p_gpu[f] - p_ref[f])) <= 1e-12 * p_ref[f].max()
+        assert np.max(np.abs(p_gpu[f] - p_ref[f])) <= 1e-7 * p_ref[f].max()
         assert np.max(np.abs(s_gpu[f] - s_ref[f])) <= 1e-5 * s_ref[f].max()
         assert p_gpu[f].sum() * g.dt == pytest.approx(e_gpu[f], rel=1e-12)
         assert s_gpu[f].sum() == pytest.approx(e_gpu[f], rel=1e-6)
