@@ -565,3 +565,48 @@ def test_status_codes_of_the_added_entry_points():
         c.adjoint_forward([z, z], np.zeros(3), 3, 1e-6, np.ones(2))
     assert ei.value.status == br.BRAHMS_E_SIZE
     c.close()
+
+
+def test_boyd_kleinman_focusing_study_on_gpu():
+    """Undepleted cw focused SHG (k_SH = 2 k_F, no walk-off) over the focusing
+    parameter xi = L/b at the optimal sigma (Boyd-Kleinman, Sec. 4): the GPU's SH
+    energy follows the driven-mode integral G(L) = (kappa/2) A0^2 int_0^L
+    e^{-i dk z} / (1 + i 2 (z - L/2) / b) dz to 1e-4 at each xi, and among the
+    sampled xi the SH power per unit length peaks at xi = 2.84."""
+    from scipy.integrate import quad
+    br = _br()
+    n_test, lam, w0 = 2.156, 1064e-9, 20e-6
+    fields = [wl.FieldParams(lam / 2, n_test), wl.FieldParams(lam, n_test)]
+    b = 2 * math.pi * n_test / lam * w0 * w0
+    # 512 um window: at xi = 5 the ends of the crystal see a 5.1 w0 beam
+    g = wl.Grid(256, 256, 1, 2.0e-6, 2.0e-6, 1e-15)
+    x, y, _ = g.axes()
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    a0 = 1e3
+    kappa_sh = 2 * math.pi * wl.D_EFF / (n_test * lam / 2)
+    dk = -2 * 0.57 / b
+    hs = {}
+    for xi in (0.5, 1.4, 2.84, 5.0):
+        L = xi * b
+        f0 = L / 2
+        q0 = 1 - 1j * 2 * f0 / b
+        a_f0 = (a0 * np.exp(-r2 / (w0 * w0 * q0)) / q0)[None]
+        nz = 400
+        s = br.Solver(g, fields, wl.D_EFF, dk)
+        s.set_fields(_dev([np.zeros_like(a_f0), a_f0]))
+        s.propagate(nz, L / nz)
+        e, _ = s.energy()
+        s.close()
+
+        def kern(z):
+            return np.exp(-1j * dk * z) / (1 + 1j * 2 * (z - f0) / b)
+
+        re_part = quad(lambda z: kern(z).real, 0, L, epsrel=1e-11, limit=400)[0]
+        im_part = quad(lambda z: kern(z).imag, 0, L, epsrel=1e-11, limit=400)[0]
+        G = (kappa_sh / 2) * a0 * a0 * abs(re_part + 1j * im_part)
+        # the SH mode exp(-2 r^2 / (w0^2 q)) / q carries int |u|^2 dx dy = pi w0^2 / 4 at every z
+        e_ref = 0.5 * wl.C0 * wl.EPS0 * n_test * G * G * (math.pi * w0 * w0 / 4) * g.dt
+        assert e[0] / e_ref - 1 == pytest.approx(0.0, abs=1e-4), (xi, e[0] / e_ref)
+        hs[xi] = e[0] / L
+    record("bk_study", xi=sorted(hs), h_over_h284=[hs[k] / hs[2.84] for k in sorted(hs)])
+    assert max(hs, key=hs.get) == 2.84
