@@ -17,6 +17,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   propagate           energy and Manley-Rowe invariants, second-order
                       self-convergence in dz
   energy              analytic Gaussian-beam/pulse energy
+  heat_load           Gaussian beam/pulse absorbed power, the linear step's
+                      own loss rate
+  thermal_solve       discrete eigenmodes, second-order convergence to a
+                      continuum solution, the discrete heat-flux balance
   adjoint_gradient    dot-product identities (linear step; RK4 against an
                       independent tangent-linear RK4), stage-phase
                       sensitivities and full gradients against central
@@ -94,6 +98,7 @@ def _load():
             lib.orc_propagate_map.restype = ctypes.c_int
             lib.orc_power_trace.argtypes = [P(_Problem), vp, dp]
             lib.orc_spectrum.argtypes = [P(_Problem), vp, dp]
+            lib.orc_heat_load.argtypes = [P(_Problem), vp, ctypes.c_double, dp]
             lib.orc_rk4_jvp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                               vp, vp, vp, vp]
             lib.orc_rk4_vjp_point.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -233,6 +238,46 @@ def spectrum(prob: _Problem, fields: Sequence[np.ndarray]) -> np.ndarray:
     out = np.zeros((prob.nf, prob.nt))
     _load().orc_spectrum(ctypes.byref(prob), a.ctypes.data, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     return out
+
+
+def heat_load(prob: _Problem, fields: Sequence[np.ndarray], rep_rate: float = 0.0) -> np.ndarray:
+    """[ny, nx] absorbed power density Q [W/m^3] (orc_heat_load)."""
+    a = _stack(fields)
+    out = np.zeros((prob.ny, prob.nx))
+    _load().orc_heat_load(ctypes.byref(prob), a.ctypes.data, float(rep_rate),
+                          out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    return out
+
+
+def thermal_matrix(nx: int, ny: int, dx: float, dy: float):
+    """The 5-point operator -(d_xx + d_yy) on the fields' (x, y) grid as a
+    sparse matrix (row index y * nx + x), with T = 0 half a cell outside the
+    window: the missing neighbour of an edge point is its mirror image -T, so
+    the edge's diagonal entry gains one more 1/d^2.  An axis of length 1 has
+    no derivative along it (Sec. 3, heat equation; the boundary reading is the
+    crystal's side faces held at the mount temperature)."""
+    import scipy.sparse as sp
+
+    def second_difference(n, d):
+        if n == 1:
+            return sp.csr_matrix((1, 1))
+        main = np.full(n, 2.0)
+        main[0] += 1.0
+        main[-1] += 1.0
+        off = np.full(n - 1, -1.0)
+        return sp.diags([off, main, off], [-1, 0, 1], format="csr") / (d * d)
+
+    return (sp.kron(sp.identity(ny), second_difference(nx, dx))
+            + sp.kron(second_difference(ny, dy), sp.identity(nx))).tocsc()
+
+
+def thermal_solve(q: np.ndarray, dx: float, dy: float, kappa_th: float) -> np.ndarray:
+    """Steady-state temperature rise T [ny, nx] [K] of -kappa_th lap T = q:
+    the stencil matrix of thermal_matrix() solved by a sparse direct solver."""
+    import scipy.sparse.linalg as spla
+    ny, nx = q.shape
+    a = thermal_matrix(nx, ny, dx, dy) * kappa_th
+    return spla.spsolve(a, np.ascontiguousarray(q, dtype=np.float64).ravel()).reshape(ny, nx)
 
 
 def problem_from(p) -> _Problem:

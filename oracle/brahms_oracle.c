@@ -508,6 +508,26 @@ void orc_spectrum(const orc_problem* pb, const cplx* fields, double* spectrum) {
   free(col);
 }
 
+/* Heat load of the thermal model (Sec. 3, the source term Q of the heat
+ * equation): the absorbed optical power density
+ *   Q(x, y) = sum_f alpha_f I_f,   I_f = 1/2 c eps0 n_f |A_f|^2,
+ * alpha_f the intensity absorption coefficient (the linear step damps the
+ * amplitude by exp(-alpha_f dz / 2)).  For nt > 1 the pulse train is
+ * time-averaged: Q = rep_rate sum_f alpha_f sum_tau I_f dt.                 */
+void orc_heat_load(const orc_problem* pb, const cplx* fields, double rep_rate, double* q) {
+  const int64_t plane = (int64_t)pb->nx * pb->ny, n = plane * pb->nt;
+  const double tavg = pb->nt > 1 ? rep_rate * pb->dt : 1.0;
+  for (int64_t i = 0; i < plane; ++i) q[i] = 0.0;
+  for (int f = 0; f < pb->nf; ++f) {
+    const double c = pb->f[f].alpha * 0.5 * ORC_C0 * ORC_EPS0 * pb->f[f].n * tavg;
+    for (int k = 0; k < pb->nt; ++k)
+      for (int64_t i = 0; i < plane; ++i) {
+        const cplx a = fields[f * n + k * plane + i];
+        q[i] += c * (creal(a) * creal(a) + cimag(a) * cimag(a));
+      }
+  }
+}
+
 /* ======================================================================== */
 /* Discrete adjoint (reverse mode) of the split-step propagation.            */
 /*                                                                            */
