@@ -135,6 +135,43 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
  * FP64 (the spectrum's transform is FP32).  Waits for the stream. */
 brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectrum);
 
+/* Thermal model (Sec. 3: the steady-state heat equation lap T = -Q / kappa
+ * solved on the fields' grid, and the temperature dependence of the phase
+ * mismatch).  Three calls:
+ *
+ * brahms_heat_accumulate adds weight * Q(x, y) of the current fields to the
+ * context's heat load [W/m^3], Q the absorbed optical power density
+ *   Q = sum_f alpha_f I_f,  I_f = 1/2 c eps0 n_f |A_f|^2,
+ * alpha_f the intensity absorption of field f (its brahms_field_params
+ * alpha, the same loss the linear step applies).  For nt > 1 the pulses are
+ * time-averaged: Q = rep_rate * sum_f alpha_f sum_tau I_f dt (rep_rate in Hz,
+ * >= 0); for nt == 1 (cw) rep_rate is ignored.  Sampling the fields at
+ * several z and choosing the weights of a quadrature rule (summing to one)
+ * gives the z-averaged load.  Asynchronous; FP64 accumulation.
+ * E_STATE without fields, E_ARG for a negative rep_rate or non-finite
+ * arguments.
+ *
+ * brahms_heat_set replaces the load with q[ny][nx] (host, W/m^3, x fastest;
+ * any finite values, negative ones being heat sinks); NULL zeroes it.
+ *
+ * brahms_thermal_map solves, in FP64, the transverse heat equation
+ *   -kappa_th (d_xx + d_yy) T = Q
+ * with the 5-point stencil on the fields' (x, y) grid and T = 0 (the mount
+ * temperature) half a cell outside the window on every side, i.e. on the
+ * crystal's side faces at x_{-1/2} and x_{nx-1/2}; with insulated end faces
+ * this is the equation of the z-averaged temperature rise under the
+ * z-averaged load.  An axis of length 1 is invariant (no derivative along
+ * it).  The solve is direct (sine-transform diagonalisation).  It installs
+ * dk_map = dkdT * T as the transverse mismatch map (replacing any map of
+ * brahms_set_dk_map; remove it with brahms_set_dk_map(ctx, NULL)) and, if
+ * temperature is not NULL, copies T [K above the mount, ny*nx doubles, x
+ * fastest] to it.  kappa_th [W/(m K)] must be > 0, dkdT [1/(m K)] finite.
+ * E_STATE if no load was accumulated or set, E_NONFINITE (map not
+ * installed) if the load is not finite.  Waits for the stream. */
+brahms_status brahms_heat_accumulate(brahms_ctx* ctx, double rep_rate, double weight);
+brahms_status brahms_heat_set(brahms_ctx* ctx, const double* q);
+brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, double* temperature);
+
 /* Current propagation distance [m] and accumulated mismatch phase [rad]. */
 brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
 

@@ -60,6 +60,9 @@ SIGNATURES = {
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_diagnostics": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_set_dk_map": (_c.c_int, [_vp, _dp]),
+    "brahms_heat_accumulate": (_c.c_int, [_vp, _c.c_double, _c.c_double]),
+    "brahms_heat_set": (_c.c_int, [_vp, _dp]),
+    "brahms_thermal_map": (_c.c_int, [_vp, _c.c_double, _c.c_double, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
     "brahms_launch_count": (_c.c_longlong, [_vp]),
     "brahms_set_option": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
@@ -232,6 +235,27 @@ class Solver:
         sp = np.zeros((self.nf, self.grid.nt))
         _check(self.ctx, load().brahms_diagnostics(self.ctx, p.ctypes.data_as(_dp), sp.ctypes.data_as(_dp)))
         return p, sp
+
+    def heat_accumulate(self, rep_rate: float = 0.0, weight: float = 1.0):
+        """Add weight * Q(x, y) of the current fields to the heat load [W/m^3]
+        (Q = sum_f alpha_f I_f, time-averaged at rep_rate [Hz] when nt > 1)."""
+        _check(self.ctx, load().brahms_heat_accumulate(self.ctx, float(rep_rate), float(weight)))
+
+    def heat_set(self, q):
+        """Replace the heat load with q [ny, nx] in W/m^3; None zeroes it."""
+        if q is None:
+            _check(self.ctx, load().brahms_heat_set(self.ctx, None))
+            return
+        a = np.ascontiguousarray(q, dtype=np.float64).reshape(self.grid.ny, self.grid.nx)
+        _check(self.ctx, load().brahms_heat_set(self.ctx, a.ctypes.data_as(_dp)))
+
+    def thermal_map(self, kappa_th: float, dkdT: float, want_temperature: bool = True):
+        """Solve -kappa_th lap_perp T = Q (T = 0 half a cell outside the window),
+        install dk_map = dkdT * T; returns T [ny, nx] in K (or None)."""
+        t = np.zeros((self.grid.ny, self.grid.nx)) if want_temperature else None
+        _check(self.ctx, load().brahms_thermal_map(self.ctx, float(kappa_th), float(dkdT),
+                                                   None if t is None else t.ctypes.data_as(_dp)))
+        return t
 
     def sync(self):
         _check(self.ctx, load().brahms_sync(self.ctx))

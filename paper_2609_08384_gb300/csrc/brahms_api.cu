@@ -139,6 +139,7 @@ void brahms_free(brahms_ctx* ctx) {
   if (ctx->ev_x) cudaEventDestroy(ctx->ev_x);
   if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
   if (ctx->adj_mem) cudaFree(ctx->adj_mem);
+  if (ctx->th_mem) cudaFree(ctx->th_mem);
   if (ctx->energy_host) cudaFreeHost(ctx->energy_host);
   delete ctx;
 }

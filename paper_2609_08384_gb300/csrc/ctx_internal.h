@@ -114,6 +114,14 @@ struct brahms_ctx {
   double adj_dz = 0.0;
   bool adj_ready = false;
   std::vector<double> adj_weights, adj_dk, adj_phis;
+  // thermal model (allocated on first use)
+  char* th_mem = nullptr;
+  double* th_heat = nullptr;   // heat load [ny][nx] W/m^3
+  double* th_temp = nullptr;   // temperature rise [ny][nx] K
+  double2* th_twx = nullptr;   // sine-transform tables (nx, ny entries)
+  double2* th_twy = nullptr;
+  int* th_bad = nullptr;       // non-finite temperature flag
+  bool have_heat = false;
 
   long long npoints() const { return (long long)nx * ny * nt; }
 };

@@ -1,0 +1,327 @@
+// Thermal model (Sec. 3: steady-state heat equation on the fields' grid and the
+// temperature dependence of the phase mismatch).
+//
+// heat_load_kernel   Q(x, y) += sum_f c_f sum_tau |A_f|^2: one pass over the
+//                    state, 64 x-points by 8 tau-lanes per CTA, FP32 squares of
+//                    four tau samples summed into FP64, lanes reduced in a
+//                    fixed order (deterministic).
+// sine_lines_kernel  the transverse Poisson solve's transforms.  With T = 0
+//                    half a cell outside the window, sin(pi k (j + 1/2) / n),
+//                    k = 1..n, are the eigenvectors of the 3-point second
+//                    difference, with eigenvalues -4 sin^2(pi k / (2n)) / d^2;
+//                    analysis along x and y, a division by the eigenvalues
+//                    and synthesis solve the 5-point system exactly.  Each
+//                    analysis or synthesis of a line is one complex FFT of
+//                    length 2n (odd extension) in FP64 shared memory: an
+//                    in-place Stockham FFT, radix 2 and 3, with one barrier
+//                    between the reads and the writes of every stage.
+#include "kernels.cuh"
+
+namespace brahms {
+
+namespace {
+
+constexpr int kHeatX = 64;    // x-points per CTA (32 pairs)
+constexpr int kHeatLanes = 8;  // tau-lanes per CTA
+constexpr int kSineThreads = 512;
+constexpr int kSineMaxB2 = 8;  // radix-2 butterflies per thread: m / 2 <= 8 * 512, m <= 8192
+constexpr int kSineMaxB3 = 2;  // radix-3 butterflies per thread: m / 3 <= 2 * 512
+constexpr int kSineMaxStages = 16;
+
+struct SineArgs {
+  double* d;
+  const double2* tw;  // n entries: e^{-2 pi i j / m}, j < m / 2, m = 2n
+  long long elem;     // stride between the entries of a line
+  long long pitch;    // stride between lines
+  int n;
+  int nst;
+  int rad[kSineMaxStages];
+};
+
+__device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// e^{-+2 pi i e / m}, 0 <= e < m, from the half table
+__device__ __forceinline__ double2 sine_tw(const double2* tw, int m, int e, bool inv) {
+  const int h = m >> 1;
+  double2 w = e < h ? tw[e] : make_double2(-tw[e - h].x, -tw[e - h].y);
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+// unnormalised DFT of buf[0..m) in place: sign -1 (forward) or +1 (inv)
+__device__ void fft64_inplace(double2* buf, const SineArgs& a, int m, bool inv) {
+  int ns = 1;
+  for (int s = 0; s < a.nst; ++s) {
+    const int R = a.rad[s];
+    const int nb = m / R;
+    const int step = m / (ns * R);
+    if (R == 2) {
+      double2 v[kSineMaxB2][2];
+#pragma unroll
+      for (int b = 0; b < kSineMaxB2; ++b) {
+        const int j = threadIdx.x + b * kSineThreads;
+        if (j < nb) {
+          const int k = j % ns;
+          v[b][0] = buf[j];
+          v[b][1] = z_mul(buf[j + nb], sine_tw(a.tw, m, k * step, inv));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int b = 0; b < kSineMaxB2; ++b) {
+        const int j = threadIdx.x + b * kSineThreads;
+        if (j < nb) {
+          const int k = j % ns;
+          const int base = (j / ns) * ns * 2 + k;
+          buf[base] = make_double2(v[b][0].x + v[b][1].x, v[b][0].y + v[b][1].y);
+          buf[base + ns] = make_double2(v[b][0].x - v[b][1].x, v[b][0].y - v[b][1].y);
+        }
+      }
+    } else {
+      double2 v[kSineMaxB3][3];
+#pragma unroll
+      for (int b = 0; b < kSineMaxB3; ++b) {
+        const int j = threadIdx.x + b * kSineThreads;
+        if (j < nb) {
+          const int k = j % ns;
+          v[b][0] = buf[j];
+          v[b][1] = z_mul(buf[j + nb], sine_tw(a.tw, m, k * step, inv));
+          v[b][2] = z_mul(buf[j + 2 * nb], sine_tw(a.tw, m, 2 * k * step, inv));
+        }
+      }
+      __syncthreads();
+      // X1,2 = x0 - (x1 + x2) / 2 -+ i s (sqrt(3) / 2) (x1 - x2), s = +1 forward, -1 inverse
+      const double h3 = inv ? -0.86602540378443864676 : 0.86602540378443864676;
+#pragma unroll
+      for (int b = 0; b < kSineMaxB3; ++b) {
+        const int j = threadIdx.x + b * kSineThreads;
+        if (j < nb) {
+          const int k = j % ns;
+          const int base = (j / ns) * ns * 3 + k;
+          const double2 x0 = v[b][0], x1 = v[b][1], x2 = v[b][2];
+          const double2 t1 = make_double2(x1.x + x2.x, x1.y + x2.y);
+          const double2 t2 = make_double2(x0.x - 0.5 * t1.x, x0.y - 0.5 * t1.y);
+          const double2 t3 = make_double2(h3 * (x1.x - x2.x), h3 * (x1.y - x2.y));
+          buf[base] = make_double2(x0.x + t1.x, x0.y + t1.y);
+          buf[base + ns] = make_double2(t2.x + t3.y, t2.y - t3.x);
+          buf[base + 2 * ns] = make_double2(t2.x - t3.y, t2.y + t3.x);
+        }
+      }
+    }
+    __syncthreads();
+    ns *= R;
+  }
+}
+
+// SYNTH false: S_k = sum_j x_j sin(pi k (j + 1/2) / n), k = 1..n, stored at k - 1.
+// SYNTH true:  x_j = sum_k (a_k / nu_k) sin(pi k (j + 1/2) / n), a_k read at k - 1,
+//              nu_k = n / 2 (k < n) or n (k = n): the inverse of the analysis.
+template <bool SYNTH>
+__global__ void __launch_bounds__(kSineThreads) sine_lines_kernel(const SineArgs a) {
+  extern __shared__ double2 zbuf[];
+  const int n = a.n, m = 2 * n;
+  double* p = a.d + (long long)blockIdx.x * a.pitch;
+  if (!SYNTH) {
+    // odd extension: y_j = x_j, y_{m-1-j} = -x_j
+    for (int j = threadIdx.x; j < n; j += kSineThreads) {
+      const double v = p[j * a.elem];
+      zbuf[j] = make_double2(v, 0.0);
+      zbuf[m - 1 - j] = make_double2(-v, 0.0);
+    }
+  } else {
+    // c_k = (a_k / nu_k) e^{i pi k / (2n)} for k = 1..n, zero elsewhere
+    for (int k = threadIdx.x; k < m; k += kSineThreads) {
+      double2 c = make_double2(0.0, 0.0);
+      if (k >= 1 && k <= n) {
+        const double b = p[(k - 1) * a.elem] / (k < n ? 0.5 * n : (double)n);
+        double sn, cs;
+        sincospi((double)k / (double)m, &sn, &cs);
+        c = make_double2(b * cs, b * sn);
+      }
+      zbuf[k] = c;
+    }
+  }
+  __syncthreads();
+  fft64_inplace(zbuf, a, m, SYNTH);
+  if (!SYNTH) {
+    // Y_k e^{-i pi k / (2n)} = -2i S_k
+    for (int k = 1 + threadIdx.x; k <= n; k += kSineThreads) {
+      double sn, cs;
+      sincospi((double)k / (double)m, &sn, &cs);
+      const double2 y = zbuf[k];
+      p[(k - 1) * a.elem] = 0.5 * (sn * y.x - cs * y.y);
+    }
+  } else {
+    for (int j = threadIdx.x; j < n; j += kSineThreads) p[j * a.elem] = zbuf[j].y;
+  }
+}
+
+__global__ void sine_twiddles_kernel(double2* tw, int n) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double sn, cs;
+  sincospi(-(double)j / (double)n, &sn, &cs);  // e^{-2 pi i j / (2n)}
+  tw[j] = make_double2(cs, sn);
+}
+
+// T-hat /= kappa mu_pq, mu_pq = 4 sin^2(pi (p+1) / (2 nx)) / dx^2 + (same in y)
+__global__ void thermal_divide_kernel(double* d, int nx, int ny, double dx, double dy, double kappa) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nx * ny) return;
+  const int p = (int)(i % nx), q = (int)(i / nx);
+  const double sx = sinpi((double)(p + 1) / (2.0 * nx));
+  double mu = 4.0 * sx * sx / (dx * dx);
+  if (ny > 1) {
+    const double sy = sinpi((double)(q + 1) / (2.0 * ny));
+    mu += 4.0 * sy * sy / (dy * dy);
+  }
+  d[i] /= kappa * mu;
+}
+
+__global__ void thermal_map_kernel(const double* __restrict__ t, long long n, double dkdT, double* dkmap, int* bad) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = t[i];
+  if (!isfinite(v)) atomicOr(bad, 1);
+  dkmap[i] = dkdT * v;
+}
+
+__global__ void __launch_bounds__(kHeatX / 2 * kHeatLanes) heat_load_kernel(const HeatArgs a) {
+  __shared__ double red[kHeatLanes][kHeatX];
+  const int xp = blockIdx.x * (kHeatX / 2) + threadIdx.x;  // x pair
+  const int x = 2 * xp;
+  const int y = blockIdx.y;
+  const long long plane = (long long)a.nx * a.ny;
+  double s0 = 0.0, s1 = 0.0;
+  if (x < a.nx) {
+    for (int f = 0; f < a.nf; ++f) {
+      const float4* p = reinterpret_cast<const float4*>(a.data + f * a.fstride + (long long)y * a.nx + x);
+      const long long ps = plane / 2;  // plane stride in float4 (nx even)
+      double f0 = 0.0, f1 = 0.0;
+      int t = threadIdx.y;
+      for (; t + 3 * kHeatLanes < a.nt; t += 4 * kHeatLanes) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = __ldcs(p + (t + u * kHeatLanes) * ps);
+        float q0 = 0.f, q1 = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          q0 = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, q0));
+          q1 = fmaf(v[u].z, v[u].z, fmaf(v[u].w, v[u].w, q1));
+        }
+        f0 += (double)q0;
+        f1 += (double)q1;
+      }
+      for (; t < a.nt; t += kHeatLanes) {
+        const float4 v = __ldcs(p + t * ps);
+        f0 += (double)fmaf(v.x, v.x, v.y * v.y);
+        f1 += (double)fmaf(v.z, v.z, v.w * v.w);
+      }
+      s0 += a.c[f] * f0;
+      s1 += a.c[f] * f1;
+    }
+  }
+  red[threadIdx.y][2 * threadIdx.x] = s0;
+  red[threadIdx.y][2 * threadIdx.x + 1] = s1;
+  __syncthreads();
+  if (threadIdx.y == 0 && x < a.nx) {
+    double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+    for (int l = 0; l < kHeatLanes; ++l) {
+      r0 += red[l][2 * threadIdx.x];
+      r1 += red[l][2 * threadIdx.x + 1];
+    }
+    double* h = a.heat + (long long)y * a.nx + x;
+    h[0] += r0;
+    h[1] += r1;
+  }
+}
+
+bool sine_plan(int n, SineArgs& a) {
+  int m = 2 * n, st = 0;
+  while (m % 2 == 0) {
+    if (st == kSineMaxStages) return false;
+    a.rad[st++] = 2;
+    m /= 2;
+  }
+  while (m % 3 == 0) {
+    if (st == kSineMaxStages) return false;
+    a.rad[st++] = 3;
+    m /= 3;
+  }
+  if (m != 1) return false;
+  a.nst = st;
+  a.n = n;
+  const int mm = 2 * n;
+  for (int s = 0; s < st; ++s) {
+    const int nb = mm / a.rad[s];
+    const int cap = (a.rad[s] == 2 ? kSineMaxB2 : kSineMaxB3) * kSineThreads;
+    if (nb > cap) return false;
+  }
+  return true;
+}
+
+template <bool SYNTH>
+cudaError_t sine_lines(double* d, const double2* tw, int n, long long elem, long long pitch, int lines,
+                       cudaStream_t s) {
+  SineArgs a{};
+  if (!sine_plan(n, a)) return cudaErrorInvalidValue;
+  a.d = d;
+  a.tw = tw;
+  a.elem = elem;
+  a.pitch = pitch;
+  const size_t smem = sizeof(double2) * 2 * (size_t)n;
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(sine_lines_kernel<SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)std::max<size_t>(smem, 48 * 1024));
+    if (e != cudaSuccess) return e;
+    configured = std::max<size_t>(smem, 48 * 1024);
+  }
+  sine_lines_kernel<SYNTH><<<lines, kSineThreads, smem, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace
+
+bool sine_length_supported(int n) {
+  if (n < 2) return false;
+  SineArgs a{};
+  return sine_plan(n, a) && sizeof(double2) * 2 * (size_t)n <= 227 * 1024;
+}
+
+cudaError_t run_sine_twiddles(double2* tw, int n, cudaStream_t s) {
+  sine_twiddles_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_heat_load(const HeatArgs& a, cudaStream_t s) {
+  if (a.nx % 2) return cudaErrorInvalidValue;
+  const dim3 grid((unsigned)((a.nx + kHeatX - 1) / kHeatX), (unsigned)a.ny);
+  heat_load_kernel<<<grid, dim3(kHeatX / 2, kHeatLanes), 0, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+cudaError_t run_thermal_solve(const ThermalArgs& a, int* nlaunch, cudaStream_t s) {
+  const long long n = (long long)a.nx * a.ny;
+  int nl = 0;
+  cudaError_t e = cudaMemcpyAsync(a.temp, a.heat, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = sine_lines<false>(a.temp, a.twx, a.nx, 1, a.nx, a.ny, s), ++nl;
+  if (e == cudaSuccess && a.ny > 1) e = sine_lines<false>(a.temp, a.twy, a.ny, a.nx, 1, a.nx, s), ++nl;
+  if (e == cudaSuccess) {
+    thermal_divide_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.temp, a.nx, a.ny, a.dx, a.dy, a.kappa);
+    e = cudaPeekAtLastError(), ++nl;
+  }
+  if (e == cudaSuccess && a.ny > 1) e = sine_lines<true>(a.temp, a.twy, a.ny, a.nx, 1, a.nx, s), ++nl;
+  if (e == cudaSuccess) e = sine_lines<true>(a.temp, a.twx, a.nx, 1, a.nx, a.ny, s), ++nl;
+  if (e == cudaSuccess) {
+    thermal_map_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a.temp, n, a.dkdT, a.dkmap, a.bad);
+    e = cudaPeekAtLastError(), ++nl;
+  }
+  *nlaunch = nl;
+  return e;
+}
+
+}  // namespace brahms

@@ -562,6 +562,31 @@ cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s);
 cudaError_t run_power_trace(const float2* data, int nx, int ny, int nt, int nf, long long fstride, double* out,
                             cudaStream_t s);
 cudaError_t run_tau_spectrum(int nt, const AxisArgs& a, double* out, cudaStream_t s);
+
+// thermal model (k_thermal.cu)
+struct HeatArgs {
+  const float2* data;
+  long long fstride;
+  int nx, ny, nt, nf;
+  double c[3];  // weight * alpha_f * 1/2 c eps0 n_f (* rep_rate dt for nt > 1)
+  double* heat;  // [ny][nx], accumulated into
+};
+cudaError_t run_heat_load(const HeatArgs& a, cudaStream_t s);
+// sine-transform tables for one axis of length n > 1: n entries
+cudaError_t run_sine_twiddles(double2* tw, int n, cudaStream_t s);
+bool sine_length_supported(int n);
+struct ThermalArgs {
+  const double* heat;  // [ny][nx] W/m^3
+  double* temp;        // [ny][nx] K, output (also the transform's work array)
+  const double2* twx;  // sine-transform tables of nx and ny
+  const double2* twy;
+  int nx, ny;
+  double dx, dy, kappa;
+  double dkdT;
+  double* dkmap;  // [ny][nx] 1/m, output
+  int* bad;       // set if a temperature is not finite
+};
+cudaError_t run_thermal_solve(const ThermalArgs& a, int* nlaunch, cudaStream_t s);
 cudaError_t run_energy(const float2* data, long long n, int nf, long long fstride, double* partial,
                        int nblocks, double* out, cudaStream_t s);
 cudaError_t run_c128_to_c64(const double2* in, float2* out, long long n, cudaStream_t s);
