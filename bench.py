@@ -373,6 +373,50 @@ def diagnostics_form(solver, problem, reps=3):
             "workload": "power trace + tau spectrum of the 3 x 256x256x512 OPG state"}
 
 
+def thermal_form(solver, problem, dev, reps=5):
+    """Thermal model: the heat load of the resident OPG state (one pass over the
+    3 x 256x256x512 fields) timed with CUDA events on the solver stream, and the
+    FP64 transverse Poisson solve with its map install (wall time per call,
+    including the 4-byte status read) on 256x256, 1024x1024 and 4096x4096."""
+    import torch
+
+    import paper_2609_08384_gb300 as br
+    from paper_2609_08384_gb300 import workloads as wl
+
+    g = problem.grid
+    st = solver.stream
+    solver.heat_accumulate(1e6, 1.0)
+    solver.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        solver.heat_accumulate(1e6, 1.0)
+    e1.record(st)
+    solver.sync()
+    us = e0.elapsed_time(e1) / reps * 1e3
+    nbytes = 8.0 * g.npoints * problem.nfields + 16.0 * g.nx * g.ny
+    out = {"heat_load_us": us, "heat_load_alg_GB_per_s": nbytes / (us / 1e6) / 1e9,
+           "heat_load_workload": "3 x 256x256x512 OPG state, one pass"}
+
+    def solve_ms(s):
+        s.thermal_map(1.0, 0.0, want_temperature=False)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            s.thermal_map(1.0, 0.0, want_temperature=False)
+        return (time.perf_counter() - t0) / reps * 1e3
+
+    out[f"solve_ms_{g.nx}x{g.ny}"] = solve_ms(solver)
+    solver.set_dk_map(None)
+    rng = np.random.default_rng(wl.SEED_BASE + 7)
+    for n in (1024, 4096):
+        gg = wl.Grid(n, n, 1, 1e-6, 1e-6, 1e-15)
+        s = br.Solver(gg, wl.shg_fields(), wl.D_EFF, 0.0, stream=torch.cuda.Stream(device=dev), device=dev)
+        s.heat_set(rng.random((n, n)) * 1e9)
+        out[f"solve_ms_{n}x{n}"] = solve_ms(s)
+        s.close()
+    return out
+
+
 def adjoint_form(dev):
     """SHG efficiency gradient on 128x128x256 over 400 steps (256-entry spectral
     phase, 400-entry mismatch profile), sqrt(nz) checkpointing: the time of the
@@ -552,16 +596,24 @@ def run_ours(args):
     nbytes = g.npoints * problem.nfields * 8
     e2e = {"value": world * units_per_step * e2e_steps / t_e2e, "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
-    diag = diagnostics_form(solver, problem) if not args.no_forms else None
-    solver.close()
+    def want(name):
+        return not args.no_forms and (args.forms is None or name in args.forms.split(","))
+
     forms = {"plain": value}
-    if not args.no_forms:
-        forms["diagnostics"] = diag
+    if want("diagnostics"):
+        forms["diagnostics"] = diagnostics_form(solver, problem)
+    if want("thermal"):
+        forms["thermal"] = thermal_form(solver, problem, dev)
+    solver.close()
+    if want("cw_focused_shg"):
         forms["cw_focused_shg"] = cw_form(dev)
-        if problem.name.startswith("opg"):
-            forms["dk_map"] = dk_map_form(dev, dev_in)
+    if want("dk_map") and problem.name.startswith("opg"):
+        forms["dk_map"] = dk_map_form(dev, dev_in)
+    if want("batched"):
         forms["batched"] = batched_form(dev)
+    if want("batched_small_grids"):
         forms["batched_small_grids"] = batched_form(dev, small=True)
+    if want("adjoint"):
         forms["adjoint"] = adjoint_form(dev)
 
     if rank != 0:
@@ -592,6 +644,9 @@ def main():
     ap.add_argument("--config", default="opg", choices=["opg", "sfg", "shg"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and adjoint forms")
+    ap.add_argument("--forms", default=None,
+                    help="comma-separated subset of the forms (diagnostics, thermal, cw_focused_shg, dk_map, "
+                         "batched, batched_small_grids, adjoint); default all")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -3,8 +3,8 @@
 //
 // heat_load_kernel   Q(x, y) += sum_f c_f sum_tau |A_f|^2: one pass over the
 //                    state, 64 x-points by 8 tau-lanes per CTA, FP32 squares of
-//                    four tau samples summed into FP64, lanes reduced in a
-//                    fixed order (deterministic).
+//                    eight tau samples summed pairwise, then into FP64; lanes
+//                    reduced in a fixed order (deterministic).
 // sine_lines_kernel  the transverse Poisson solve's transforms.  With T = 0
 //                    half a cell outside the window, sin(pi k (j + 1/2) / n),
 //                    k = 1..n, are the eigenvectors of the 3-point second
@@ -23,6 +23,7 @@ namespace {
 
 constexpr int kHeatX = 64;    // x-points per CTA (32 pairs)
 constexpr int kHeatLanes = 8;  // tau-lanes per CTA
+constexpr int kHeatU = 8;      // tau samples per thread and iteration
 constexpr int kSineThreads = 512;
 constexpr int kSineMaxB2 = 8;  // radix-2 butterflies per thread: m / 2 <= 8 * 512, m <= 8192
 constexpr int kSineMaxB3 = 2;  // radix-3 butterflies per thread: m / 3 <= 2 * 512
@@ -194,25 +195,35 @@ __global__ void __launch_bounds__(kHeatX / 2 * kHeatLanes) heat_load_kernel(cons
   const int x = 2 * xp;
   const int y = blockIdx.y;
   const long long plane = (long long)a.nx * a.ny;
+  const long long ps = plane / 2;  // plane stride in float4 (nx even)
   double s0 = 0.0, s1 = 0.0;
   if (x < a.nx) {
-    for (int f = 0; f < a.nf; ++f) {
+#pragma unroll
+    for (int f = 0; f < 3; ++f) {
+      if (f >= a.nf) break;
       const float4* p = reinterpret_cast<const float4*>(a.data + f * a.fstride + (long long)y * a.nx + x);
-      const long long ps = plane / 2;  // plane stride in float4 (nx even)
       double f0 = 0.0, f1 = 0.0;
       int t = threadIdx.y;
-      for (; t + 3 * kHeatLanes < a.nt; t += 4 * kHeatLanes) {
-        float4 v[4];
+      // kHeatU tau samples in flight per thread; their squares summed pairwise in FP32
+      for (; t + (kHeatU - 1) * kHeatLanes < a.nt; t += kHeatU * kHeatLanes) {
+        float4 v[kHeatU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldcs(p + (t + u * kHeatLanes) * ps);
-        float q0 = 0.f, q1 = 0.f;
+        for (int u = 0; u < kHeatU; ++u) v[u] = __ldcs(p + (t + u * kHeatLanes) * ps);
+        float q0[kHeatU], q1[kHeatU];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          q0 = fmaf(v[u].x, v[u].x, fmaf(v[u].y, v[u].y, q0));
-          q1 = fmaf(v[u].z, v[u].z, fmaf(v[u].w, v[u].w, q1));
+        for (int u = 0; u < kHeatU; ++u) {
+          q0[u] = fmaf(v[u].x, v[u].x, v[u].y * v[u].y);
+          q1[u] = fmaf(v[u].z, v[u].z, v[u].w * v[u].w);
         }
-        f0 += (double)q0;
-        f1 += (double)q1;
+#pragma unroll
+        for (int w = kHeatU / 2; w > 0; w >>= 1)
+#pragma unroll
+          for (int u = 0; u < w; ++u) {
+            q0[u] += q0[u + w];
+            q1[u] += q1[u + w];
+          }
+        f0 += (double)q0[0];
+        f1 += (double)q1[0];
       }
       for (; t < a.nt; t += kHeatLanes) {
         const float4 v = __ldcs(p + t * ps);
