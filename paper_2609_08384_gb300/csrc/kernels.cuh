@@ -79,6 +79,15 @@ template <int N>
 __host__ __device__ constexpr int xpass_smem_floats2(int nf) {
   return 6 * nf + nf * xpass_rows<N>() * XchRow::pitch(N);
 }
+// resident CTAs the x-pass asks the register allocator for: 6 (80 registers)
+// where six CTAs' shared memory fits in an SM and rows are at most 256 long
+// (no spills there); otherwise 4 (128 registers)
+template <int N, int F>
+__host__ __device__ constexpr int xpass_min_blocks() {
+  return xpass_threads<N>() > 128                                                          ? 1
+         : (N <= 256 && 6 * (xpass_smem_floats2<N>(F) * 8 + 1024) <= 228 * 1024) ? 6
+                                                                                          : 4;
+}
 
 // Strided pencils: tiles of TX neighbouring columns (128-byte rows up to
 // N = 1024) times the plan's T threads per pencil.
@@ -360,7 +369,7 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
 // MAP: per-point stage phases from a transverse mismatch map (p.emap);
 // REC: record the half steps' input states (p.rec_b, p.rec_a)
 template <int NX, int F, bool MAP, bool REC = false>
-__global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 128 ? 4 : 1)
+__global__ void __launch_bounds__(xpass_threads<NX>(), xpass_min_blocks<NX, F>())
     xpass_kernel(const XPassArgs p) {
   constexpr int THREADS = xpass_threads<NX>();
   extern __shared__ float4 sm4[];
