@@ -266,8 +266,10 @@ brahms_status brahms_batch_set_fields(brahms_batch* b, int index, const void* co
  * item for the x-, y- and tau-passes (1..64). */
 brahms_status brahms_batch_set_granularity(brahms_batch* b, int shape, int gx, int gy, int gt);
 
-/* Autotune the schedule: per shape the tiles per item (1, 2, 4), then CTAs
- * per SM (1, 2), each timed on the whole batch with every instance capped at
+/* Autotune the schedule: per shape the tiles per item (one of 1, 2, 4, 8, 16
+ * for all three passes, then each pass's doubled or halved while that helps,
+ * within 1..64), then CTAs per SM (1, 2), each timed on the whole batch with
+ * every instance capped at
  * tune_steps steps; instance fields are restored afterwards.  Waits for the
  * stream.  *best_ms (nullable) receives the best capped run time. */
 brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms);

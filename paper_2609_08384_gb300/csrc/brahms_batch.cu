@@ -773,7 +773,8 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
   for (int sh = 0; sh < kNumShapes && st == BRAHMS_OK; ++sh) {
     if (!present[sh]) continue;
     int keep[3] = {b->gran[sh][0], b->gran[sh][1], b->gran[sh][2]};
-    for (int g : {1, 2, 4}) {
+    // one granularity for all three passes, then a per-pass search
+    for (int g : {1, 2, 4, 8, 16}) {
       if (g == keep[0] && g == keep[1] && g == keep[2]) continue;
       b->gran[sh][0] = b->gran[sh][1] = b->gran[sh][2] = g;
       float ms = 0.f;
@@ -782,6 +783,22 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
       if (ms < cur) {
         cur = ms;
         keep[0] = keep[1] = keep[2] = g;
+      }
+    }
+    // per pass: keep doubling (then halving) while the batch gets faster
+    for (int k = 0; k < 3 && st == BRAHMS_OK; ++k) {
+      for (int up = 1; up >= 0 && st == BRAHMS_OK; --up) {
+        for (;;) {
+          const int g = up ? keep[k] * 2 : keep[k] / 2;
+          if (g < 1 || g > 64) break;
+          for (int j = 0; j < 3; ++j) b->gran[sh][j] = keep[j];
+          b->gran[sh][k] = g;
+          float ms = 0.f;
+          st = trial(&ms);
+          if (st != BRAHMS_OK || ms >= cur) break;
+          cur = ms;
+          keep[k] = g;
+        }
       }
     }
     b->gran[sh][0] = keep[0];
