@@ -610,3 +610,49 @@ def test_boyd_kleinman_focusing_study_on_gpu():
         hs[xi] = e[0] / L
     record("bk_study", xi=sorted(hs), h_over_h284=[hs[k] / hs[2.84] for k in sorted(hs)])
     assert max(hs, key=hs.get) == 2.84
+
+
+def test_boyd_kleinman_convergence_in_dz():
+    """Convergence of cw focused SHG at the Boyd-Kleinman optimum (xi = 2.84,
+    sigma = -0.57) to the driven-mode integral as dz is halved: the split step
+    is second order (Sec. 3.1), so the SH energy's error falls about 4x per
+    halving until it reaches the FP32 floor."""
+    from scipy.integrate import quad
+    br = _br()
+    n_test, lam, w0 = 2.156, 1064e-9, 20e-6
+    fields = [wl.FieldParams(lam / 2, n_test), wl.FieldParams(lam, n_test)]
+    b = 2 * math.pi * n_test / lam * w0 * w0
+    g = wl.Grid(256, 256, 1, 2.0e-6, 2.0e-6, 1e-15)
+    x, y, _ = g.axes()
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    a0 = 1e3
+    kappa_sh = 2 * math.pi * wl.D_EFF / (n_test * lam / 2)
+    dk = -2 * 0.57 / b
+    L = 2.84 * b
+    f0 = L / 2
+    q0 = 1 - 1j * 2 * f0 / b
+    a_f0 = (a0 * np.exp(-r2 / (w0 * w0 * q0)) / q0)[None]
+
+    def kern(z):
+        return np.exp(-1j * dk * z) / (1 + 1j * 2 * (z - f0) / b)
+
+    re_part = quad(lambda z: kern(z).real, 0, L, epsrel=1e-12, limit=400)[0]
+    im_part = quad(lambda z: kern(z).imag, 0, L, epsrel=1e-12, limit=400)[0]
+    G = (kappa_sh / 2) * a0 * a0 * abs(re_part + 1j * im_part)
+    e_ref = 0.5 * wl.C0 * wl.EPS0 * n_test * G * G * (math.pi * w0 * w0 / 4) * g.dt
+    energies = {}
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    for nz in (12, 24, 48, 96, 768):
+        s.set_fields(_dev([np.zeros_like(a_f0), a_f0]))
+        s.propagate(nz, L / nz)
+        e, _ = s.energy()
+        energies[nz] = e[0]
+    s.close()
+    coarse = (12, 24, 48, 96)
+    # self-convergence against the finest run isolates the dz error from the window/FP32 floor
+    errs = [abs(energies[nz] / energies[768] - 1) for nz in coarse]
+    to_closed_form = [abs(energies[nz] / e_ref - 1) for nz in coarse + (768,)]
+    record("bk_convergence_dz", nz=list(coarse) + [768], rel_err_closed_form=to_closed_form, rel_err_vs_768=errs)
+    slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(1.7 < sl < 2.3 for sl in slopes), (errs, slopes)
+    assert to_closed_form[-1] < 1e-4
