@@ -108,9 +108,10 @@ def _load():
             lib.orc_nonlinear_step_adjoint.argtypes = [P(_Problem), vp, vp, ctypes.c_double, ctypes.c_double,
                                                        ctypes.c_double, dp]
             lib.orc_adjoint_gradient.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp,
-                                                 ctypes.c_int, dp, dp, dp]
+                                                 ctypes.c_int, dp, dp, dp, dp]
             lib.orc_adjoint_gradient.restype = ctypes.c_double
-            lib.orc_objective.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, dp]
+            lib.orc_objective.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, dp,
+                                          dp]
             lib.orc_objective.restype = ctypes.c_double
             _lib = lib
     return _lib
@@ -331,25 +332,32 @@ def spectral_phase(prob, field, phi, sign=+1):
     return a
 
 
-def objective(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1):
+def _map(prob, dk_map):
+    return None if dk_map is None else np.ascontiguousarray(dk_map, dtype=np.float64).reshape(prob.ny, prob.nx)
+
+
+def objective(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None):
     a = _stack(fields)
     dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
     w = np.ascontiguousarray(weights, dtype=np.float64)
     ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    m = _map(prob, dk_map)
     return float(_load().orc_objective(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
-                                       _dptr(ph), int(phi_field), _dptr(w)))
+                                       _dptr(ph), int(phi_field), _dptr(w), _dptr(m)))
 
 
-def adjoint_gradient(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1):
+def adjoint_gradient(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None):
     """J = sum_f w_f sum |A_f(L)|^2 and its gradient with respect to the
     spectral phase phi (centred order, applied to field phi_field) and the
-    per-step mismatch.  Returns (J, grad_phi or None, grad_dk)."""
+    per-step mismatch, optionally under a transverse mismatch map dk_map
+    [ny, nx].  Returns (J, grad_phi or None, grad_dk)."""
     a = _stack(fields)
     dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
     w = np.ascontiguousarray(weights, dtype=np.float64)
     ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
     gphi = None if phi is None else np.zeros(prob.nt)
     gdk = np.zeros(nz)
+    m = _map(prob, dk_map)
     J = _load().orc_adjoint_gradient(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
-                                     _dptr(ph), int(phi_field), _dptr(w), _dptr(gphi), _dptr(gdk))
+                                     _dptr(ph), int(phi_field), _dptr(w), _dptr(gphi), _dptr(gdk), _dptr(m))
     return float(J), gphi, gdk

@@ -711,13 +711,16 @@ typedef struct {
   cplx* g;       /* adjoint in/out */
   double kap[3];
   double phi_a, dk, h;
+  double z_a;            /* distance of the half step's start from z = 0 (for the map) */
+  const double* dk_map;  /* transverse mismatch map [ny][nx] or NULL */
   double* part;  /* [slot][3] partial stage sensitivities */
   int64_t chunk; /* points per slot (fixed, so the sums do not depend on threads) */
 } vjp_job;
 
 static void vjp_slots(void* p, int64_t s0, int64_t s1) {
   vjp_job* j = (vjp_job*)p;
-  int64_t n = (int64_t)j->pb->nx * j->pb->ny * j->pb->nt;
+  const int64_t plane = (int64_t)j->pb->nx * j->pb->ny;
+  int64_t n = plane * j->pb->nt;
   int nf = j->pb->nf;
   for (int64_t s = s0; s < s1; ++s) {
     double acc[3] = {0, 0, 0};
@@ -729,7 +732,9 @@ static void vjp_slots(void* p, int64_t s0, int64_t s1) {
         x[f] = j->x[f * n + i];
         gy[f] = j->g[f * n + i];
       }
-      orc_rk4_vjp_point(nf, j->kap, j->phi_a, j->dk, j->h, x, gy, gx, acc);
+      /* with a map the point's phase is Phi_a + m z_a at the start and grows at dk + m */
+      const double m = j->dk_map ? j->dk_map[i % plane] : 0.0;
+      orc_rk4_vjp_point(nf, j->kap, j->phi_a + m * j->z_a, j->dk + m, j->h, x, gy, gx, acc);
       for (int f = 0; f < nf; ++f) j->g[f * n + i] = gx[f];
     }
     for (int k = 0; k < 3; ++k) j->part[s * 3 + k] = acc[k];
@@ -737,9 +742,11 @@ static void vjp_slots(void* p, int64_t s0, int64_t s1) {
 }
 
 /* g <- adjoint of N(h) (RK4 from phi_a over h) at the forward input x;
- * sens[0..2] = dJ/dPhi at the three stage points (start, middle, end). */
-void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, double phi_a, double dk, double h,
-                                double* sens) {
+ * sens[0..2] = dJ/dPhi at the three stage points (start, middle, end).
+ * With a transverse map (dk_map non-NULL) the half step starts at distance
+ * z_a and each point follows its own phase, as in orc_nonlinear_step_map. */
+void orc_nonlinear_step_adjoint_map(const orc_problem* pb, const cplx* x, cplx* g, double phi_a, double dk, double h,
+                                    double z_a, const double* dk_map, double* sens) {
   int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
   const int64_t chunk = 4096;
   int64_t slots = (n + chunk - 1) / chunk;
@@ -752,6 +759,8 @@ void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, d
   j.phi_a = phi_a;
   j.dk = dk;
   j.h = h;
+  j.z_a = z_a;
+  j.dk_map = dk_map;
   j.part = part;
   j.chunk = chunk;
   parallel_for(slots, vjp_slots, &j);
@@ -761,13 +770,20 @@ void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, d
   free(part);
 }
 
+void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, double phi_a, double dk, double h,
+                                double* sens) {
+  orc_nonlinear_step_adjoint_map(pb, x, g, phi_a, dk, h, 0.0, NULL, sens);
+}
+
 /* Gradient of J = sum_f w[f] sum |A_f(L)|^2 with respect to the spectral phase
  * phi (applied to field phi_field at z = 0, centred order, nt entries; NULL
- * for none) and to the per-step mismatch dk_steps[0..nz-1].  Forward states
- * of every step are kept (the oracle is for small grids).  Returns J. */
+ * for none) and to the per-step mismatch dk_steps[0..nz-1], under the
+ * transverse map dk_map (NULL for none; the map itself is not a parameter).
+ * Forward states of every step are kept (the oracle is for small grids).
+ * Returns J. */
 double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
                             const double* phi, int phi_field, const double* w, double* grad_phi,
-                            double* grad_dk) {
+                            double* grad_dk, const double* dk_map) {
   int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
   int nf = pb->nf;
   int64_t sz = n * nf;
@@ -779,7 +795,10 @@ double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz
   for (int j = 0; j < nz; ++j) {
     memcpy(st + (j + 1) * sz, st + j * sz, sizeof(cplx) * sz);
     double ph = phis[j];
-    orc_propagate(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph);
+    if (dk_map)
+      orc_propagate_map(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph, j * dz, dk_map);
+    else
+      orc_propagate(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph);
     phis[j + 1] = ph;
   }
   /* objective and its gradient at z = L */
@@ -798,13 +817,18 @@ double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz
   for (int j = nz - 1; j >= 0; --j) {
     const cplx* aj = st + j * sz;
     double dk = dk_steps[j];
+    const double zj = j * dz;
     /* a2 = L(N_A(A_j)) */
     memcpy(a2, aj, sizeof(cplx) * sz);
-    orc_nonlinear_step(pb, a2, phis[j], dk, 0.5 * dz);
+    if (dk_map)
+      orc_nonlinear_step_map(pb, a2, phis[j], dk, 0.5 * dz, zj, dk_map);
+    else
+      orc_nonlinear_step(pb, a2, phis[j], dk, 0.5 * dz);
     orc_linear_step(pb, a2, dz);
-    orc_nonlinear_step_adjoint(pb, a2, g, phis[j] + dk * 0.5 * dz, dk, 0.5 * dz, S + j * 6 + 3);
+    orc_nonlinear_step_adjoint_map(pb, a2, g, phis[j] + dk * 0.5 * dz, dk, 0.5 * dz, zj + 0.5 * dz, dk_map,
+                                   S + j * 6 + 3);
     orc_linear_step_adjoint(pb, g, dz);
-    orc_nonlinear_step_adjoint(pb, aj, g, phis[j], dk, 0.5 * dz, S + j * 6);
+    orc_nonlinear_step_adjoint_map(pb, aj, g, phis[j], dk, 0.5 * dz, zj, dk_map, S + j * 6);
   }
   /* dJ/d dk_j: stage offsets within step j, plus dz for every later stage */
   if (grad_dk) {
@@ -855,14 +879,17 @@ double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz
 
 /* J only (for finite differences): the same forward map as above. */
 double orc_objective(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
-                     const double* phi, int phi_field, const double* w) {
+                     const double* phi, int phi_field, const double* w, const double* dk_map) {
   int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
   int nf = pb->nf;
   cplx* a = (cplx*)malloc(sizeof(cplx) * n * nf);
   memcpy(a, fields_in, sizeof(cplx) * n * nf);
   if (phi) orc_spectral_phase(pb, a + phi_field * n, phi, +1);
   double ph = 0.0;
-  orc_propagate(pb, a, nz, dz, dk_steps, &ph);
+  if (dk_map)
+    orc_propagate_map(pb, a, nz, dz, dk_steps, &ph, 0.0, dk_map);
+  else
+    orc_propagate(pb, a, nz, dz, dk_steps, &ph);
   double J = 0.0;
   for (int f = 0; f < nf; ++f)
     for (int64_t i = 0; i < n; ++i) J += w[f] * (creal(a[f * n + i]) * creal(a[f * n + i]) + cimag(a[f * n + i]) * cimag(a[f * n + i]));

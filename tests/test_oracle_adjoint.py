@@ -138,3 +138,47 @@ def test_three_field_gradient_dk_matches_differences():
         fd = (oracle.objective(prob, ins, nz, dz, dk, w, phi + e, 0) -
               oracle.objective(prob, ins, nz, dz, dk, w, phi - e, 0)) / 2e-3
         assert abs(gphi[p] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (p, gphi[p], fd)
+
+
+@pytest.mark.parametrize("three", [False, True])
+def test_gradient_under_mismatch_map_matches_differences(three):
+    """A transverse mismatch map (fan-out ramp plus a bump) changes every
+    point's stage phases; the adjoint under the map matches central
+    differences of the map objective for the per-step mismatch and the
+    spectral phase, and differs clearly from the map-free gradient."""
+    rng = np.random.default_rng(47 + three)
+    if three:
+        g = wl.Grid(8, 8, 16, 6 * UM, 6 * UM, 30 * FS)
+        f = _fields3()
+        x, y, t = g.axes()
+        env = np.exp(-(x[None, None] ** 2 + y[None, :, None] ** 2) / (15 * UM) ** 2 - (t[:, None, None] / (120 * FS)) ** 2)
+        ins = [8e7 * env + 0j, 2e7 * env * np.exp(0.3j), 1e6 * (rng.standard_normal(env.shape) + 0j)]
+        nz, dz, w, pf = 12, 30 * UM, np.array([0.0, 1.0, 0.5]), 0
+        dk = rng.normal(300.0, 200.0, nz)
+    else:
+        g, f, ins = _small_shg()
+        x, y, _ = g.axes()
+        nz, dz, pf = 16, 40 * UM, 1
+        wF = np.sum(np.abs(ins[1]) ** 2)
+        w = np.array([f[0].n / (f[1].n * wF), 0.0])
+        dk = rng.normal(0, 0.1, nz) / MM
+    prob = oracle.make_problem(g, f, wl.D_EFF)
+    m = 4e6 * x[None, :] + 3e3 * np.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / (12 * UM) ** 2) + 0 * y[:, None]
+    phi = rng.normal(0, 0.2, g.nt)
+    J, gphi, gdk = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf, dk_map=m)
+    assert J == pytest.approx(oracle.objective(prob, ins, nz, dz, dk, w, phi, pf, dk_map=m), rel=1e-14)
+    hk = 1.0
+    for j in (0, nz // 2, nz - 1):
+        e = np.zeros(nz)
+        e[j] = hk
+        fd = (oracle.objective(prob, ins, nz, dz, dk + e, w, phi, pf, dk_map=m) -
+              oracle.objective(prob, ins, nz, dz, dk - e, w, phi, pf, dk_map=m)) / (2 * hk)
+        assert abs(gdk[j] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (j, gdk[j], fd)
+    for p in (0, g.nt // 2 - 1, g.nt - 1):
+        e = np.zeros(g.nt)
+        e[p] = 1e-3
+        fd = (oracle.objective(prob, ins, nz, dz, dk, w, phi + e, pf, dk_map=m) -
+              oracle.objective(prob, ins, nz, dz, dk, w, phi - e, pf, dk_map=m)) / 2e-3
+        assert abs(gphi[p] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (p, gphi[p], fd)
+    _, gphi0, gdk0 = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf)
+    assert np.linalg.norm(gdk - gdk0) > 0.1 * np.linalg.norm(gdk)
