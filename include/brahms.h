@@ -120,8 +120,8 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction);
  * every step's Delta k, so the nonlinear step's phase becomes
  *   Phi(x, y, z) = Phi_j + Delta k_j (z - z_j) + dk_map(x, y) z,
  * z measured from the last brahms_set_fields.  The library copies the map;
- * NULL removes it.  E_ARG for non-finite entries.  The adjoint refuses a
- * context with a map (E_STATE). */
+ * NULL removes it.  E_ARG for non-finite entries.  The adjoint propagates
+ * and differentiates under the map (the map itself is not a parameter). */
 brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
 
 /* Diagnostics of the current fields (the Sec. 6 power formula resolved in

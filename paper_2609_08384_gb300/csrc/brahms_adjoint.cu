@@ -70,7 +70,6 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
                                      const double* weights, int checkpoint_interval, double* J) {
   if (!ctx) return BRAHMS_E_ARG;
   if (ctx->ny < 2 || ctx->nt < 2) return fail(ctx, BRAHMS_E_SIZE, "the adjoint needs ny >= 2 and nt >= 2");
-  if (ctx->have_map) return fail(ctx, BRAHMS_E_STATE, "the adjoint does not take a transverse mismatch map");
   if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
     return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
   if (phi && (phi_field < 0 || phi_field >= ctx->nf)) return fail(ctx, BRAHMS_E_ARG, "phi_field out of range");
@@ -194,6 +193,14 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
       r.phiB = ctx->adj_phis[b - 1] + r.dkB * 0.5 * dz;
     }
     r.partial = ctx->adj_part;
+    r.ny = ctx->ny;
+    if (ctx->have_map) {
+      // stage factors of step b-1's B half and step b's A half (distances from z = 0)
+      r.emap = ctx->emap_dev;
+      const brahms_status sm = enqueue_map_tables(ctx, b > 0 ? ctx->adj_phis[b - 1] : 0.0, b > 0 ? dk_at(b - 1) : 0.0,
+                                                  (b - 1) * dz, ctx->adj_phis[b], dk_at(b), b * dz, dz);
+      if (sm != BRAHMS_OK) return sm;
+    }
     long long ncta = 0;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_adjoint(nx, nf, r, &ncta, ctx->stream); }));
     double* sA = xa ? ctx->adj_sens + (size_t)b * 6 : nullptr;
@@ -211,6 +218,8 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
       x.data = ctx->adj_work;
       x.phiA = ctx->adj_phis[j0];
       x.dkA = dk_at(j0);
+      brahms_status sm = enqueue_map_tables(ctx, 0.0, 0.0, j0 * dz, x.phiA, x.dkA, j0 * dz, dz);
+      if (sm != BRAHMS_OK) return sm;
       BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, x, ctx->stream); }));
     }
     for (int j = j0; j < j1; ++j) {
@@ -225,6 +234,8 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
       x.dkA = dk_at(j + 1);
       x.rec_b = recB + (size_t)(j - j0) * nf * n;
       x.rec_a = last ? nullptr : recA + (size_t)(j + 1 - j0) * nf * n;
+      s2 = enqueue_map_tables(ctx, x.phiB, x.dkB, j * dz, x.phiA, x.dkA, (j + 1) * dz, dz);
+      if (s2 != BRAHMS_OK) return s2;
       BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_record(nx, nf, x, ctx->stream); }));
     }
     // reverse through boundaries j1 .. j0 + 1, each followed by the linear

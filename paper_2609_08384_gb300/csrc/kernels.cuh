@@ -291,41 +291,40 @@ __device__ __forceinline__ void xpass_tile(const XPassArgs& p, long long tile, c
       float2 a[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) a[f] = myrow[f * ROWS * PITCH + off];
-      if constexpr (MAP) {
-        // e^{i Phi(x, y, z_s)} = T V^s at this point, for the B and A stages
-        if (mode != XM_NL_FIRST) {
+      // MAP: e^{i Phi(x, y, z_s)} = T V^s at this point, for the B and A stages
+      if (mode != XM_NL_FIRST) {
+        if constexpr (REC) {
+          if (p.rec_b && act) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) p.rec_b[f * p.fstride + row * NX + pos] = a[f];
+          }
+        }
+        if constexpr (MAP) {
           float2 e3[3];
           const float2 v = __ldg(emap + nxy + pos);
           e3[0] = __ldg(emap + pos);
           e3[1] = cmul(e3[0], v);
           e3[2] = cmul(e3[1], v);
           rk4<F>(a, e3, p.kh, p.kh2);
+        } else {
+          rk4<F>(a, coef, p.kh, p.kh2);
         }
-        if (mode != XM_NL_LAST) {
+      }
+      if (mode != XM_NL_LAST) {
+        if constexpr (REC) {
+          if (p.rec_a && act) {
+#pragma unroll
+            for (int f = 0; f < F; ++f) p.rec_a[f * p.fstride + row * NX + pos] = a[f];
+          }
+        }
+        if constexpr (MAP) {
           float2 e3[3];
           const float2 v = __ldg(emap + 3 * nxy + pos);
           e3[0] = __ldg(emap + 2 * nxy + pos);
           e3[1] = cmul(e3[0], v);
           e3[2] = cmul(e3[1], v);
           rk4<F>(a, e3, p.kh, p.kh2);
-        }
-      } else {
-        if (mode != XM_NL_FIRST) {
-          if constexpr (REC) {
-            if (p.rec_b && act) {
-#pragma unroll
-              for (int f = 0; f < F; ++f) p.rec_b[f * p.fstride + row * NX + pos] = a[f];
-            }
-          }
-          rk4<F>(a, coef, p.kh, p.kh2);
-        }
-        if (mode != XM_NL_LAST) {
-          if constexpr (REC) {
-            if (p.rec_a && act) {
-#pragma unroll
-              for (int f = 0; f < F; ++f) p.rec_a[f * p.fstride + row * NX + pos] = a[f];
-            }
-          }
+        } else {
           rk4<F>(a, coef + 3, p.kh, p.kh2);
         }
       }
@@ -604,6 +603,7 @@ cudaError_t run_c64_to_c128(const float2* in, double2* out, long long n, cudaStr
 // adjoint recomputation and reverse x-pass (k_xadj.cu)
 // x-pass that also records the states entering its half steps (a.rec_b, a.rec_a)
 cudaError_t run_xpass_record(int nx, int nf, const XPassArgs& a, cudaStream_t s);
+cudaError_t run_xpass_record_map(int nx, int nf, const XPassArgs& a, cudaStream_t s);
 // Reverse of one x-pass boundary: the adjoint g, in (kx, y, tau) when
 // from_k (else real space), goes through the inverse x-FFT, the reverse of
 // the A half step at state xa (if xa), the reverse of the B half step at
@@ -620,8 +620,13 @@ struct XAdjArgs {
   double phiA, dkA, phiB, dkB, h;  // phase and mismatch at the start of each half step; h = dz/2
   float kh[3];                     // kappa_f h (1/2 on the SH equation for two fields)
   double* partial;
+  // transverse mismatch map: the per-(x, y) stage phase factors of this
+  // boundary's B and A half steps [4][ny][nx] (as in XPassArgs), or NULL
+  const float2* emap;
+  int ny;
 };
 cudaError_t run_xpass_adjoint(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s);
+cudaError_t run_xpass_adjoint_map(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s);
 // sensA[k] = sum_c partial[c][k], sensB[k] = sum_c partial[c][3 + k] (either may be NULL)
 cudaError_t run_sens_boundary(const double* partial, long long ncta, double* sensA, double* sensB, cudaStream_t s);
 long long xpass_adjoint_ctas(int nx, long long rows);

@@ -1,0 +1,28 @@
+// Launcher of the recording forward x-pass (the plain x-pass that also writes
+// the real-space states entering its B and A half steps), shared by the
+// map-free (k_xrec.cu) and mismatch-map (k_xrec_map.cu) instantiations.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace brahms {
+
+template <int NX, int F, bool MAP>
+cudaError_t launch_record(const XPassArgs& a, cudaStream_t s) {
+  constexpr int ROWS = xpass_rows<NX>();
+  constexpr int THREADS = xpass_threads<NX>();
+  const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(xpass_kernel<NX, F, MAP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const long long grid = (a.rows + ROWS - 1) / ROWS;
+  if (grid <= 0) return cudaSuccess;
+  xpass_kernel<NX, F, MAP, true><<<(unsigned)grid, THREADS, smem, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+}  // namespace brahms

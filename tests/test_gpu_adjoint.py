@@ -36,9 +36,11 @@ def _shg_case(n, nt, nz, dz, seed, intensity=3e13):
     return g, f, ins, phi, dk
 
 
-def _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, phi_field=1):
+def _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, phi_field=1, dk_map=None):
     import paper_2609_08384_gb300 as br
     s = br.Solver(g, f, wl.D_EFF, 0.0)
+    if dk_map is not None:
+        s.set_dk_map(dk_map)
     J = s.adjoint_forward([torch.from_numpy(a).cuda() for a in ins], dk, nz, dz, w, phi=phi, phi_field=phi_field,
                           checkpoint_interval=interval)
     gphi, gdk = s.adjoint_backward(1.0)
@@ -168,3 +170,58 @@ def test_field_streams_do_not_change_the_gradient():
         s.close()
     assert out[0][0] == out[1][0]
     assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def _fanout_map(g, slope=4e6, bump=3e3, width=30 * wl.UM):
+    x, y, _ = g.axes()
+    return slope * x[None, :] + bump * np.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / width**2)
+
+
+@pytest.mark.parametrize("three", [False, True])
+def test_gradient_under_mismatch_map_matches_oracle(three):
+    """A fan-out map plus a bump: the recomputation, the recording x-pass and
+    the reverse x-pass take per-point stage phases; gradients against the
+    oracle's adjoint under the same map."""
+    if three:
+        g = wl.Grid(24, 16, 32, 6 * wl.UM, 6 * wl.UM, 30 * wl.FS)
+        f = [wl.FieldParams(wl.LAM_P, wl.N_P, delta=1e-10, k2=2e-25, rho=2e-3),
+             wl.FieldParams(wl.LAM_S, wl.N_S, k2=1e-25),
+             wl.FieldParams(wl.LAM_I, wl.N_I, delta=-1e-10, k2=5e-26, rho=1e-3, alpha=20.0)]
+        x, y, t = g.axes()
+        env = np.exp(-(x[None, None] ** 2 + y[None, :, None] ** 2) / (25 * wl.UM) ** 2 - (t[:, None, None] / (150 * wl.FS)) ** 2)
+        rng = np.random.default_rng(9)
+        ins = [(8e7 * env).astype(np.complex64), (2e7 * env * np.exp(0.3j)).astype(np.complex64),
+               (1e6 * rng.standard_normal(env.shape)).astype(np.complex64)]
+        nz, dz, pf = 16, 25 * wl.UM, 0
+        dk = rng.normal(300.0, 200.0, nz)
+        phi = rng.normal(0, 0.2, g.nt)
+        w = np.array([0.0, 1e-15, 5e-16])
+        m = _fanout_map(g, slope=2e7, bump=2e4, width=15 * wl.UM)
+    else:
+        nz = 60
+        dz = 5 * wl.UM * (400 / nz) * 0.25
+        g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 83)
+        w = np.array([f[0].n / (f[1].n * float(np.sum(np.abs(ins[1].astype(np.complex128)) ** 2))), 0.0])
+        pf = 1
+        m = _fanout_map(g)
+    J, gphi, gdk = _gpu_grad(g, f, ins, phi, dk, nz, dz, w, phi_field=pf, dk_map=m)
+    prob = oracle.make_problem(g, f, wl.D_EFF)
+    ins128 = [a.astype(np.complex128) for a in ins]
+    Jr, gphi_r, gdk_r = oracle.adjoint_gradient(prob, ins128, nz, dz, dk, w, phi=phi, phi_field=pf, dk_map=m)
+    assert abs(J / Jr - 1) < 1e-4
+    assert rel_l2(gphi, gphi_r) < GRAD_TOL
+    assert rel_l2(gdk, gdk_r) < GRAD_TOL
+    # the map is felt: the map-free oracle gradient is far off
+    _, _, gdk0 = oracle.adjoint_gradient(prob, ins128, nz, dz, dk, w, phi=phi, phi_field=pf)
+    assert rel_l2(gdk0, gdk_r) > 20 * GRAD_TOL
+
+
+def test_checkpoint_interval_does_not_change_the_gradient_under_a_map():
+    nz, dz = 30, 20 * wl.UM
+    g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 61)
+    w = np.array([1e-20, 0.0])
+    m = _fanout_map(g)
+    res = [_gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=k, dk_map=m) for k in (0, 7, 1)]
+    for J, gp, gd in res[1:]:
+        assert J == res[0][0]
+        assert np.array_equal(gp, res[0][1]) and np.array_equal(gd, res[0][2])

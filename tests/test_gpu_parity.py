@@ -457,7 +457,7 @@ def test_dk_map_matches_oracle(shape, nf):
 def test_dk_map_zero_uniform_and_cleared():
     """A zero map reproduces the map-free run to FP32 rounding, a uniform map
     c the run with dk + c; clearing the map restores the map-free result bit
-    for bit; the adjoint refuses a map."""
+    for bit; under a zero map the adjoint gives the map-free gradient."""
     br = _br()
     g, fields, init, _ = _map_case(32, 16, 32, 3, 5)
     dz, dk = 8 * wl.UM, 700.0
@@ -486,10 +486,16 @@ def test_dk_map_zero_uniform_and_cleared():
     cleared = s.get_fields()
     for f in range(3):
         assert np.array_equal(cleared[f], plain[f])
-    s.set_dk_map(np.zeros((16, 32)))
-    with pytest.raises(br.BrahmsError):
-        s.adjoint_forward(_dev(init), np.zeros(4), 4, dz, np.ones(3))
+    w = np.array([0.0, 1e-15, 5e-16])
+    dks = np.full(6, dk)
+    grads = []
+    for m in (np.zeros((16, 32)), None):
+        s.set_dk_map(m)
+        J = s.adjoint_forward(_dev(init), dks, 6, dz, w)
+        grads.append((J, s.adjoint_backward(1.0)[1]))
     s.close()
+    assert grads[0][0] == pytest.approx(grads[1][0], rel=1e-6)
+    assert rel_l2(grads[0][1], grads[1][1]) < 1e-4
 
 
 EXTREME = [(4096, 2, 2), (2, 4096, 2), (2, 2, 4096), (768, 6, 4), (6, 768, 4), (4, 6, 768), (2, 2, 2)]
