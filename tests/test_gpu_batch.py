@@ -89,7 +89,7 @@ def test_batch_repeat_is_deterministic_and_tuner_keeps_results():
             assert np.array_equal(x[f], y[f])
     c, _, sched = _run_batch(probs, inputs, tune=True)
     for s in sched:
-        assert s[0] in (1, 2, 4) and s[3] in (1, 2)
+        assert all(v in (1, 2, 4, 8, 16, 32, 64) for v in s[:3]) and s[3] in (1, 2)
     for x, y in zip(a, c):
         for f in range(2):
             assert np.array_equal(x[f], y[f])  # the schedule changes who computes, not what
