@@ -454,11 +454,26 @@ def adjoint_form(dev):
     e0.record(stream)
     torch.cuda.synchronize(dev)
     ms_fwd, ms_bwd, ms_plain = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[3].elapsed_time(e0)
+    # every step recorded in the forward (2 nz states, 54 GB here): no recomputation in the backward
+    s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase, checkpoint_interval=-1)
+    s.adjoint_backward(1.0)
+    torch.cuda.synchronize(dev)
+    e[0].record(stream)
+    s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase, checkpoint_interval=-1)
+    e[1].record(stream)
+    s.adjoint_backward(1.0)
+    e[2].record(stream)
+    torch.cuda.synchronize(dev)
+    ms_fwd_all, ms_bwd_all = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
     s.close()
     units = float(p.grid.npoints * 2 * p.nz)
     return {"value": units / ((ms_fwd + ms_bwd) / 1e3), "unit": UNIT, "eta": J,
             "ms_forward_checkpointed": ms_fwd, "ms_backward": ms_bwd, "ms_plain_forward": ms_plain,
             "gradient_cost_vs_plain_forward": (ms_fwd + ms_bwd) / ms_plain,
+            "store_all": {"value": units / ((ms_fwd_all + ms_bwd_all) / 1e3), "ms_forward_recording": ms_fwd_all,
+                          "ms_backward": ms_bwd_all,
+                          "gradient_cost_vs_plain_forward": (ms_fwd_all + ms_bwd_all) / ms_plain,
+                          "state_memory_GB": 2 * p.nz * p.grid.npoints * 2 * 8 / 1e9},
             "workload": "SHG 128x128x256, 400 steps of 5 um, d eta / d(phi[256], dk[400])"}
 
 

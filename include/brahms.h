@@ -216,9 +216,13 @@ long long brahms_launch_count(const brahms_ctx* ctx);
  * the linear step reversed as IDFT3(conj(P) DFT3), each RK4 half step in
  * reverse mode with its stages recomputed, and the mismatch through the RK4
  * stage phases Phi(z) = Phi_j + dk_j (z - z_j).  Memory: the forward keeps a
- * checkpoint every K steps (K = ceil(sqrt(nz)) when checkpoint_interval <= 0)
- * and the backward recomputes K step states per segment; the library
- * allocates (ceil(nz/K) + K + 2) field states plus small tables for it.
+ * checkpoint every K steps (K = ceil(sqrt(nz)) when checkpoint_interval == 0,
+ * K = checkpoint_interval when > 0) and the backward recomputes each segment,
+ * recording the 2K states entering its steps' two half steps; the library
+ * allocates (ceil(nz/K) + 2K + 2) field states plus small tables for it.
+ * checkpoint_interval < 0: the forward records all 2 nz such states itself
+ * (2 nz + 3 field states; on a large-memory GPU usually affordable) and the
+ * backward recomputes nothing.  The gradient is bit-identical either way.
  * ---------------------------------------------------------------------- */
 
 /* Set the fields (as brahms_set_fields), apply the phase (phi may be NULL),

@@ -6,7 +6,9 @@
 // default) while the fused propagation runs.  Backward: segments are visited
 // last to first.  Each is recomputed from its checkpoint with the recording
 // x-pass, which keeps the states entering every B half step (a2_j) and every
-// A half step (A_j).  The adjoint then runs the forward's pass structure in
+// A half step (A_j).  With a negative checkpoint interval the forward itself
+// runs the recording x-pass over all nz steps (2 nz states of memory) and the
+// backward recomputes nothing.  The adjoint then runs the forward's pass structure in
 // reverse: at each boundary b between steps b-1 and b one reverse x-pass
 // (inverse x-FFT, reverse of N_A at A_b, reverse of N_B at a2_{b-1}, forward
 // x-FFT), then the adjoint of the linear step, IDFT3(conj(P) DFT3), as the
@@ -21,6 +23,56 @@
 using namespace brahms_host;
 
 namespace {
+
+// y-forward, tau-propagator (conjugated for the adjoint) and y-inverse on data
+brahms_status linear_yty(brahms_ctx* ctx, float2* data, bool adjoint) {
+  brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2);
+  ay.data = data;
+  at.data = data;
+  at.conj_p = adjoint ? 1 : 0;
+  if (use_field_streams(ctx)) return enqueue_linear_split(ctx, ay, at);
+  BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
+  BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
+  BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));
+  return BRAHMS_OK;
+}
+
+// Steps j0 .. j1-1 from the real-space state in data (the state entering
+// step j0's A half step) in the forward's pass structure, with the recording
+// x-pass: a2_j (entering step j's B half step) goes to recB[j - j0] and A_j
+// (entering step j's A half step, j > j0) to recA[j - j0].  Needs adj_nz,
+// adj_dk and adj_phis.
+brahms_status record_steps(brahms_ctx* ctx, float2* data, int j0, int j1, double dz, float2* recB, float2* recA) {
+  const int nx = ctx->nx, nf = ctx->nf;
+  const long long n = ctx->npoints();
+  auto dk_at = [&](int j) { return j < ctx->adj_nz ? ctx->adj_dk[j] : ctx->dk; };
+  {
+    brahms::XPassArgs x = xargs(ctx, brahms::XM_NL_FIRST, dz);
+    x.data = data;
+    x.phiA = ctx->adj_phis[j0];
+    x.dkA = dk_at(j0);
+    brahms_status sm = enqueue_map_tables(ctx, 0.0, 0.0, j0 * dz, x.phiA, x.dkA, j0 * dz, dz);
+    if (sm != BRAHMS_OK) return sm;
+    BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, x, ctx->stream); }));
+  }
+  for (int j = j0; j < j1; ++j) {
+    brahms_status s2 = linear_yty(ctx, data, false);
+    if (s2 != BRAHMS_OK) return s2;
+    const bool last = j == j1 - 1;
+    brahms::XPassArgs x = xargs(ctx, last ? brahms::XM_NL_LAST : brahms::XM_NL_MID, dz);
+    x.data = data;
+    x.phiB = ctx->adj_phis[j];
+    x.dkB = dk_at(j);
+    x.phiA = ctx->adj_phis[j + 1];
+    x.dkA = dk_at(j + 1);
+    x.rec_b = recB + (size_t)(j - j0) * nf * n;
+    x.rec_a = last ? nullptr : recA + (size_t)(j + 1 - j0) * nf * n;
+    s2 = enqueue_map_tables(ctx, x.phiB, x.dkB, j * dz, x.phiA, x.dkA, (j + 1) * dz, dz);
+    if (s2 != BRAHMS_OK) return s2;
+    BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_record(nx, nf, x, ctx->stream); }));
+  }
+  return BRAHMS_OK;
+}
 
 brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
   const size_t state = sizeof(float2) * (size_t)ctx->nf * (size_t)ctx->npoints();
@@ -76,8 +128,10 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
   if (phi)
     for (int i = 0; i < ctx->nt; ++i)
       if (!std::isfinite(phi[i])) return fail(ctx, BRAHMS_E_ARG, "phi has non-finite entries");
-  const int K = checkpoint_interval > 0 ? std::min(checkpoint_interval, nz)
-                                        : std::max(1, (int)std::ceil(std::sqrt((double)nz)));
+  const bool store_all = checkpoint_interval < 0;
+  const int K = store_all ? nz
+                          : (checkpoint_interval > 0 ? std::min(checkpoint_interval, nz)
+                                                     : std::max(1, (int)std::ceil(std::sqrt((double)nz))));
   const int nseg = (nz + K - 1) / K;
   brahms_status s = adj_alloc(ctx, nz, K, nseg);
   if (s != BRAHMS_OK) return s;
@@ -107,18 +161,8 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
     at.scale_lo = (float)(inv - (double)at.scale);
     BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
   }
-  for (int seg = 0; seg < nseg; ++seg) {
-    BR_CK(cudaMemcpyAsync(ctx->adj_ckpt + (size_t)seg * ctx->nf * n, ctx->state, sizeof(float2) * ctx->nf * n,
-                          cudaMemcpyDeviceToDevice, ctx->stream));
-    s = brahms_propagate(ctx, std::min(K, nz - seg * K), dz);
-    if (s != BRAHMS_OK) return s;
-  }
-  s = finish_with_check(ctx);
-  if (s != BRAHMS_OK) return s;
-  double j = 0.0;
-  for (int f = 0; f < ctx->nf; ++f) j += weights[f] * ctx->energy_host[f];
-  if (J) *J = j;
   // bookkeeping for the reverse sweep (Phi_j exactly as brahms_propagate accumulates it)
+  ctx->adj_ready = false;
   ctx->adj_nz = nz;
   ctx->adj_K = K;
   ctx->adj_nseg = nseg;
@@ -133,6 +177,31 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
     ph += dk[i] * dz;
   }
   ctx->adj_phis[nz] = ph;
+  ctx->adj_store_all = store_all;
+  if (store_all) {
+    // the forward records every step's B and A inputs; A_0 is the checkpoint
+    BR_CK(cudaMemcpyAsync(ctx->adj_ckpt, ctx->state, sizeof(float2) * ctx->nf * n, cudaMemcpyDeviceToDevice,
+                          ctx->stream));
+    s = build_tables(ctx, dz);
+    if (s != BRAHMS_OK) return s;
+    s = record_steps(ctx, ctx->state, 0, nz, dz, ctx->adj_seg, ctx->adj_seg + (size_t)K * ctx->nf * n);
+    if (s != BRAHMS_OK) return s;
+    ctx->phi = ph;
+    ctx->step += nz;
+    ctx->z += nz * dz;
+  } else {
+    for (int seg = 0; seg < nseg; ++seg) {
+      BR_CK(cudaMemcpyAsync(ctx->adj_ckpt + (size_t)seg * ctx->nf * n, ctx->state, sizeof(float2) * ctx->nf * n,
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+      s = brahms_propagate(ctx, std::min(K, nz - seg * K), dz);
+      if (s != BRAHMS_OK) return s;
+    }
+  }
+  s = finish_with_check(ctx);
+  if (s != BRAHMS_OK) return s;
+  double j = 0.0;
+  for (int f = 0; f < ctx->nf; ++f) j += weights[f] * ctx->energy_host[f];
+  if (J) *J = j;
   ctx->adj_ready = true;
   return BRAHMS_OK;
 }
@@ -150,7 +219,6 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
   for (int f = 0; f < nf; ++f) sc[f] = (float)(2.0 * ctx->adj_weights[f] * gscale);
   BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_scale_fields(ctx->state, ctx->adj_g, n, nf, n, sc, ctx->stream); }));
   const brahms::XPassArgs base = xargs(ctx, brahms::XM_NL_FIRST, dz);
-  const brahms::AxisArgs ay0 = aargs(ctx, 1), at0 = aargs(ctx, 2);
   brahms_status st = build_tables(ctx, dz);
   if (st != BRAHMS_OK) return st;
   auto dk_at = [&](int j) { return j < nz ? ctx->adj_dk[j] : ctx->dk; };
@@ -158,19 +226,6 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
   // (a2_j), A[j - j0] enters step j's A half step (A_j, j > j0)
   float2* recB = ctx->adj_seg;
   float2* recA = ctx->adj_seg + (size_t)K * nf * n;
-  // y-forward, tau-propagator (conjugated in reverse) and y-inverse on data
-  const bool split = use_field_streams(ctx);
-  auto yty = [&](float2* data, bool adjoint) -> brahms_status {
-    brahms::AxisArgs ay = ay0, at = at0;
-    ay.data = data;
-    at.data = data;
-    at.conj_p = adjoint ? 1 : 0;
-    if (split) return enqueue_linear_split(ctx, ay, at);
-    BR_CK(launch(ctx, 1, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, false, ay, ctx->stream); }));
-    BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(ctx->nt, at, ctx->stream); }));
-    BR_CK(launch(ctx, 3, 1, [&] { return brahms::run_axis_fft(ctx->ny, 1, true, ay, ctx->stream); }));
-    return BRAHMS_OK;
-  };
   // reverse x-pass at boundary b (xa: A_b or NULL, xb: a2_{b-1} or NULL)
   auto reverse_x = [&](int b, const float2* xa, const float2* xb) -> brahms_status {
     brahms::XAdjArgs r{};
@@ -211,32 +266,12 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
   for (int seg = nseg - 1; seg >= 0; --seg) {
     const int j0 = seg * K, j1 = std::min(nz, j0 + K);
     // recompute the segment from its checkpoint, recording a2_j and A_j
-    BR_CK(cudaMemcpyAsync(ctx->adj_work, ctx->adj_ckpt + (size_t)seg * nf * n, sbytes, cudaMemcpyDeviceToDevice,
-                          ctx->stream));
-    {
-      brahms::XPassArgs x = base;
-      x.data = ctx->adj_work;
-      x.phiA = ctx->adj_phis[j0];
-      x.dkA = dk_at(j0);
-      brahms_status sm = enqueue_map_tables(ctx, 0.0, 0.0, j0 * dz, x.phiA, x.dkA, j0 * dz, dz);
-      if (sm != BRAHMS_OK) return sm;
-      BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, x, ctx->stream); }));
-    }
-    for (int j = j0; j < j1; ++j) {
-      brahms_status s2 = yty(ctx->adj_work, false);
+    // (already recorded by a forward that stored every step)
+    if (!ctx->adj_store_all) {
+      BR_CK(cudaMemcpyAsync(ctx->adj_work, ctx->adj_ckpt + (size_t)seg * nf * n, sbytes, cudaMemcpyDeviceToDevice,
+                            ctx->stream));
+      brahms_status s2 = record_steps(ctx, ctx->adj_work, j0, j1, dz, recB, recA);
       if (s2 != BRAHMS_OK) return s2;
-      const bool last = j == j1 - 1;
-      brahms::XPassArgs x = xargs(ctx, last ? brahms::XM_NL_LAST : brahms::XM_NL_MID, dz);
-      x.data = ctx->adj_work;
-      x.phiB = ctx->adj_phis[j];
-      x.dkB = dk_at(j);
-      x.phiA = ctx->adj_phis[j + 1];
-      x.dkA = dk_at(j + 1);
-      x.rec_b = recB + (size_t)(j - j0) * nf * n;
-      x.rec_a = last ? nullptr : recA + (size_t)(j + 1 - j0) * nf * n;
-      s2 = enqueue_map_tables(ctx, x.phiB, x.dkB, j * dz, x.phiA, x.dkA, (j + 1) * dz, dz);
-      if (s2 != BRAHMS_OK) return s2;
-      BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_record(nx, nf, x, ctx->stream); }));
     }
     // reverse through boundaries j1 .. j0 + 1, each followed by the linear
     // adjoint of the step before it
@@ -247,7 +282,7 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
       const float2* xb = recB + (size_t)(b - 1 - j0) * nf * n;
       brahms_status s2 = reverse_x(b, xa, xb);
       if (s2 != BRAHMS_OK) return s2;
-      s2 = yty(ctx->adj_g, true);
+      s2 = linear_yty(ctx, ctx->adj_g, true);
       if (s2 != BRAHMS_OK) return s2;
     }
   }

@@ -113,6 +113,7 @@ struct brahms_ctx {
   int adj_nz = 0, adj_K = 0, adj_nseg = 0, adj_phi_field = -1;
   double adj_dz = 0.0;
   bool adj_ready = false;
+  bool adj_store_all = false;  // the forward recorded every step (no recomputation)
   std::vector<double> adj_weights, adj_dk, adj_phis;
   // thermal model (allocated on first use)
   char* th_mem = nullptr;

@@ -225,3 +225,18 @@ def test_checkpoint_interval_does_not_change_the_gradient_under_a_map():
     for J, gp, gd in res[1:]:
         assert J == res[0][0]
         assert np.array_equal(gp, res[0][1]) and np.array_equal(gd, res[0][2])
+
+
+@pytest.mark.parametrize("with_map", [False, True])
+def test_store_all_forward_gives_the_same_gradient(with_map):
+    """checkpoint_interval < 0: the forward records every step and the backward
+    recomputes nothing; J and both gradients are bit-identical to the
+    checkpointed run."""
+    nz, dz = 30, 20 * wl.UM
+    g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 62)
+    w = np.array([1e-20, 0.0])
+    m = _fanout_map(g) if with_map else None
+    ref = _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, dk_map=m)
+    got = _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=-1, dk_map=m)
+    assert got[0] == ref[0]
+    assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
