@@ -24,7 +24,8 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
   adjoint_gradient    dot-product identities (linear step; RK4 against an
                       independent tangent-linear RK4), stage-phase
                       sensitivities and full gradients against central
-                      finite differences of objective()
+                      finite differences of objective(), with and without
+                      a transverse mismatch map
 """
 from __future__ import annotations
 
