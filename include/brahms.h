@@ -176,10 +176,13 @@ brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, 
 brahms_status brahms_get_z(const brahms_ctx* ctx, double* z, double* phi);
 
 /* Per-kernel timing with CUDA events on the context stream.  enable != 0
- * starts recording (and clears previous records); enable == 0 stops.  With
- * ms/launches non-NULL the accumulated device time [ms] and launch count of
- * each kernel kind (0 x-pass, 1 y-pass forward, 2 tau-pass, 3 y-pass inverse,
- * 4 other) are written to the first nkinds entries; this waits for the stream. */
+ * starts recording (and clears previous records): enable == 1 brackets every
+ * launch, enable = k > 1 every k-th launch of each kernel kind (the events
+ * cost about 2 us of device time each); enable == 0 stops.  With
+ * ms/launches non-NULL the accumulated device time [ms] and count of the
+ * timed launches of each kernel kind (0 x-pass, 1 y-pass forward, 2 tau-pass,
+ * 3 y-pass inverse, 4 other) are written to the first nkinds entries; this
+ * waits for the stream. */
 brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* launches, int nkinds);
 
 /* Implementation options; every setting computes identical numbers.

@@ -269,10 +269,14 @@ class Solver:
         _check(self.ctx, load().brahms_get_z(self.ctx, ctypes.byref(z), ctypes.byref(phi)))
         return z.value, phi.value
 
-    def timing(self, enable: bool):
+    def timing(self, enable: bool, every: int = 1):
+        """Start (enable) or stop per-kernel CUDA-event timing; every > 1 times
+        every every-th launch of each kind.  Returns (ms, timed launches) per
+        kind accumulated so far."""
         ms = np.zeros(5)
         n = np.zeros(5, dtype=np.int64)
-        _check(self.ctx, load().brahms_timing(self.ctx, int(enable), ms.ctypes.data_as(_dp),
+        flag = (max(1, int(every)) if enable else 0)
+        _check(self.ctx, load().brahms_timing(self.ctx, flag, ms.ctypes.data_as(_dp),
                                               n.ctypes.data_as(_llp), 5))
         return ms, n
 

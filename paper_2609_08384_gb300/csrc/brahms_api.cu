@@ -380,7 +380,9 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
     for (int k = 0; k < kKinds; ++k) {
       ctx->kind_ms[k] = 0.0;
       ctx->kind_n[k] = 0;
+      ctx->kind_seen[k] = 0;
     }
+    ctx->timing_every = enable > 1 ? enable : 1;
   }
   ctx->timing = enable != 0;
   return BRAHMS_OK;

@@ -91,8 +91,10 @@ struct brahms_ctx {
   std::vector<double> dk_profile;
   std::string err;
   long long launches = 0;
-  // timing
+  // timing: events around every timing_every-th launch of each kind
   bool timing = false;
+  int timing_every = 1;
+  long long kind_seen[brahms_host::kKinds]{};
   std::vector<TimedLaunch> timed;
   std::vector<cudaEvent_t> event_pool;
   double kind_ms[brahms_host::kKinds]{};
@@ -161,14 +163,15 @@ inline cudaEvent_t take_event(brahms_ctx* c) {
 template <class Fn>
 inline cudaError_t launch_on(brahms_ctx* c, cudaStream_t st, int kind, int nlaunch, Fn fn) {
   cudaEvent_t a = nullptr, b = nullptr;
-  if (c->timing) {
+  const bool timed = c->timing && (c->kind_seen[kind]++ % c->timing_every) == 0;
+  if (timed) {
     a = take_event(c);
     b = take_event(c);
     if (a && b) cudaEventRecord(a, st);
   }
   cudaError_t e = fn();
   c->launches += nlaunch;
-  if (c->timing && a && b) {
+  if (timed && a && b) {
     cudaEventRecord(b, st);
     c->timed.push_back({kind, a, b});
   }
