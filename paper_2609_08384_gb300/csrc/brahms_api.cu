@@ -209,8 +209,8 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
     if (s != BRAHMS_OK) return s;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, a, ctx->stream); }));
   }
-  // measured on GB300: 4.5 % faster on 128x128x256 (three fields), 1.6 %
-  // slower on 256x256x512, where each field's passes already fill the GPU
+  // per-field streams for the y/tau/y passes only when the option asks for
+  // them (off by default: a gain on 128x128x256 with three fields only)
   const bool split = use_field_streams(ctx);
   for (int i = 0; i < nz; ++i, ++j) {
     const double dkj = dk_of_step(ctx, j);
