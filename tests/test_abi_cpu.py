@@ -49,3 +49,29 @@ def test_status_strings_without_gpu(lib):
     assert b.value >= 3 * 256 * 256 * 512 * 8
     assert lib.brahms_workspace_size(100, 256, 512, 3, ctypes.byref(b)) == 2  # E_SIZE
     assert lib.brahms_workspace_size(256, 256, 512, 4, ctypes.byref(b)) == 1  # E_ARG
+
+
+CTX_CALLS = ["brahms_set_fields", "brahms_set_dk_profile", "brahms_propagate", "brahms_get_fields", "brahms_energy",
+             "brahms_sync", "brahms_transform", "brahms_set_dk_map", "brahms_diagnostics", "brahms_heat_accumulate",
+             "brahms_heat_set", "brahms_thermal_map", "brahms_get_z", "brahms_timing", "brahms_set_option",
+             "brahms_adjoint_forward", "brahms_adjoint_backward"]
+
+
+def test_null_context_is_an_argument_error_without_gpu(lib):
+    """Every entry point that takes a context returns BRAHMS_E_ARG for a NULL
+    context before any device work (so it is safe without a GPU)."""
+    import paper_2609_08384_gb300 as br
+    for name in CTX_CALLS:
+        restype, argtypes = br.SIGNATURES[name]
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = restype, argtypes
+        args = [None]
+        for t in argtypes[1:]:
+            args.append(0.0 if t is ctypes.c_double else (0 if t in (ctypes.c_int, ctypes.c_longlong) else None))
+        assert fn(*args) == 1, name
+    fn = lib.brahms_get_option
+    fn.restype, fn.argtypes = ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]
+    assert fn(None, 1) == -1
+    fn = lib.brahms_launch_count
+    fn.restype, fn.argtypes = ctypes.c_longlong, [ctypes.c_void_p]
+    assert fn(None) == 0
