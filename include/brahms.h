@@ -162,10 +162,11 @@ brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectru
  * this is the equation of the z-averaged temperature rise under the
  * z-averaged load.  An axis of length 1 is invariant (no derivative along
  * it).  The solve is direct (sine-transform diagonalisation).  It installs
- * dk_map = dkdT * T as the transverse mismatch map (replacing any map of
- * brahms_set_dk_map; remove it with brahms_set_dk_map(ctx, NULL)) and, if
- * temperature is not NULL, copies T [K above the mount, ny*nx doubles, x
- * fastest] to it.  kappa_th [W/(m K)] must be > 0, dkdT [1/(m K)] finite.
+ * dk_map = M + dkdT * T as the transverse mismatch map, M the map last given
+ * to brahms_set_dk_map (a fan-out grating, say; zero if none); a later
+ * brahms_set_dk_map replaces both terms, brahms_set_dk_map(ctx, NULL)
+ * removes them.  If temperature is not NULL, it copies T [K above the
+ * mount, ny*nx doubles, x fastest] to it.  kappa_th [W/(m K)] must be > 0, dkdT [1/(m K)] finite.
  * E_STATE if no load was accumulated or set, E_NONFINITE (map not
  * installed) if the load is not finite.  Waits for the stream. */
 brahms_status brahms_heat_accumulate(brahms_ctx* ctx, double rep_rate, double weight);

@@ -108,6 +108,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
   ctx->diag_dev = (double*)(ctx->ws + ctx->L.diag);
   ctx->dkmap_dev = (double*)(ctx->ws + ctx->L.dkmap);
+  ctx->usermap_dev = (double*)(ctx->ws + ctx->L.usermap);
   ctx->emap_dev = (float2*)(ctx->ws + ctx->L.emap);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
@@ -318,14 +319,17 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
   if (!ctx) return BRAHMS_E_ARG;
   if (!dk_map) {
     ctx->have_map = false;
+    ctx->have_user_map = false;
     return BRAHMS_OK;
   }
   const size_t n = (size_t)ctx->nx * ctx->ny;
   for (size_t i = 0; i < n; ++i)
     if (!std::isfinite(dk_map[i])) return fail(ctx, BRAHMS_E_ARG, "dk_map has non-finite entries");
   BR_CK(cudaMemcpyAsync(ctx->dkmap_dev, dk_map, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  BR_CK(cudaMemcpyAsync(ctx->usermap_dev, ctx->dkmap_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
   BR_CK(cudaStreamSynchronize(ctx->stream));
   ctx->have_map = true;
+  ctx->have_user_map = true;
   return BRAHMS_OK;
 }
 

@@ -6,6 +6,11 @@
 
 using namespace brahms_host;
 
+namespace brahms {
+// k_thermal.cu: dkmap += base
+cudaError_t run_map_add(double* dkmap, const double* base, long long n, cudaStream_t s);
+}  // namespace brahms
+
 namespace {
 
 brahms_status thermal_alloc(brahms_ctx* ctx) {
@@ -103,6 +108,10 @@ brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, 
   int nl = 0;
   BR_CK(launch(ctx, 4, 0, [&] { return brahms::run_thermal_solve(a, &nl, ctx->stream); }));
   ctx->launches += nl;
+  if (ctx->have_user_map)
+    BR_CK(launch(ctx, 4, 1, [&] {
+      return brahms::run_map_add(ctx->dkmap_dev, ctx->usermap_dev, (long long)ctx->nx * ctx->ny, ctx->stream);
+    }));
   int bad = 0;
   BR_CK(cudaMemcpyAsync(&bad, ctx->th_bad, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   if (temperature)

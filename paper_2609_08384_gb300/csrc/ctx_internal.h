@@ -23,7 +23,7 @@ constexpr int kKinds = 5;
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, dkmap, emap, total;
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, dkmap, usermap, emap, total;
 };
 
 inline Layout make_layout(int nx, int ny, int nt, int nf) {
@@ -47,6 +47,7 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.err = take(sizeof(int));
   L.diag = take(sizeof(double) * 2 * nt * nf);
   L.dkmap = take(sizeof(double) * nx * ny);
+  L.usermap = take(sizeof(double) * nx * ny);
   L.emap = take(sizeof(float2) * 4 * nx * ny);
   L.total = off;
   return L;
@@ -74,9 +75,11 @@ struct brahms_ctx {
   double *partial = nullptr, *energy_dev = nullptr;
   double* energy_host = nullptr;  // pinned, nf entries + the device error word
   double* diag_dev = nullptr;     // diagnostics: power [nf][nt], spectrum [nf][nt]
-  double* dkmap_dev = nullptr;    // transverse mismatch map [ny][nx] (1/m)
+  double* dkmap_dev = nullptr;    // transverse mismatch map [ny][nx] (1/m) in effect
+  double* usermap_dev = nullptr;  // the map of brahms_set_dk_map (the thermal map adds to it)
   float2* emap_dev = nullptr;     // its stage phase factors for one x-pass [4][ny][nx]
   bool have_map = false;
+  bool have_user_map = false;
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns

@@ -315,6 +315,19 @@ cudaError_t run_heat_load(const HeatArgs& a, cudaStream_t s) {
   return cudaPeekAtLastError();
 }
 
+namespace {
+__global__ void map_add_kernel(double* __restrict__ dkmap, const double* __restrict__ base, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dkmap[i] += base[i];
+}
+}  // namespace
+
+// dkmap += base (the static map under the thermal one)
+cudaError_t run_map_add(double* dkmap, const double* base, long long n, cudaStream_t s) {
+  map_add_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dkmap, base, n);
+  return cudaPeekAtLastError();
+}
+
 cudaError_t run_thermal_solve(const ThermalArgs& a, int* nlaunch, cudaStream_t s) {
   const long long n = (long long)a.nx * a.ny;
   int nl = 0;

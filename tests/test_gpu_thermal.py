@@ -167,6 +167,40 @@ def test_thermal_map_drives_the_mismatch_map():
     assert np.linalg.norm(plain[0] - want[0]) / np.linalg.norm(want[0]) > 1e-2
 
 
+def test_thermal_map_adds_to_a_static_map():
+    """A fan-out grating map M set by set_dk_map stays under the thermal map:
+    the propagation runs with M + dkdT T, as the oracle's under the same sum."""
+    br = _br()
+    fields = [wl.FieldParams(wl.LAM_SH, wl.N_SH, alpha=30.0), wl.FieldParams(wl.LAM_F, wl.N_F, alpha=12.0)]
+    g = wl.Grid(64, 48, 1, 3e-6, 3e-6, 1e-15)
+    x, y, _ = g.axes()
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    a_f = (3e7 * np.exp(-r2 / (25e-6) ** 2))[None].astype(np.complex128)
+    f0 = [np.zeros_like(a_f), a_f]
+    m = np.tile(4e6 * x, (g.ny, 1))
+    rng = np.random.default_rng(5)
+    q = 1e12 * np.exp(-r2 / (30e-6) ** 2) + 1e10 * rng.random((g.ny, g.nx))
+    kap, nz, dz, dk = 4.6, 40, 50e-6, 100.0
+    t_orc = oracle.thermal_solve(q, g.dx, g.dy, kap)
+    dkdT = 2.0 / (t_orc.max() * nz * dz)
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    want, _ = oracle.propagate_map(prob, f0, nz, dz, dk, m + dkdT * t_orc)
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map(m)
+    s.heat_set(q)
+    s.thermal_map(kap, dkdT)
+    s.set_fields(_dev(f0))
+    s.propagate(nz, dz)
+    got = [np.asarray(a) for a in s.get_fields()]
+    s.close()
+    for f in range(2):
+        err = np.linalg.norm(got[f] - want[f]) / np.linalg.norm(want[f])
+        assert err < 1e-4, (f, err)
+    # without the static map the result is clearly different
+    alt, _ = oracle.propagate_map(prob, f0, nz, dz, dk, dkdT * t_orc)
+    assert np.linalg.norm(alt[0] - want[0]) / np.linalg.norm(want[0]) > 1e-2
+
+
 def test_thermal_status_codes():
     br = _br()
     g = wl.Grid(16, 8, 4, 2e-6, 2e-6, 10e-15)
