@@ -470,9 +470,16 @@ def adjoint_form(dev):
     return {"value": units / ((ms_fwd + ms_bwd) / 1e3), "unit": UNIT, "eta": J,
             "ms_forward_checkpointed": ms_fwd, "ms_backward": ms_bwd, "ms_plain_forward": ms_plain,
             "gradient_cost_vs_plain_forward": (ms_fwd + ms_bwd) / ms_plain,
+            # bytes moved by design per grid point, field and step (the per-segment
+            # checkpoint copies left out): forward 4 passes (64 B); backward the
+            # recording recomputation (64 B + 2 writes of 8 B) and the reverse
+            # passes (64 B + 2 reads of 8 B)
+            "moved_GB_per_s_design": 224.0 * units / ((ms_fwd + ms_bwd) / 1e3) / 1e9,
             "store_all": {"value": units / ((ms_fwd_all + ms_bwd_all) / 1e3), "ms_forward_recording": ms_fwd_all,
                           "ms_backward": ms_bwd_all,
                           "gradient_cost_vs_plain_forward": (ms_fwd_all + ms_bwd_all) / ms_plain,
+                          # recording forward (80 B) and reverse passes (80 B)
+                          "moved_GB_per_s_design": 160.0 * units / ((ms_fwd_all + ms_bwd_all) / 1e3) / 1e9,
                           "state_memory_GB": 2 * p.nz * p.grid.npoints * 2 * 8 / 1e9},
             "workload": "SHG 128x128x256, 400 steps of 5 um, d eta / d(phi[256], dk[400])"}
 
