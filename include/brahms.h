@@ -135,7 +135,7 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
  * FP64 (the spectrum's transform is FP32).  Waits for the stream. */
 brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectrum);
 
-/* Thermal model (Sec. 3: the steady-state heat equation lap T = -Q / kappa
+/* Thermal model (Sec. 4.1: the steady-state heat equation lap T = -Q / kappa
  * solved on the fields' grid, and the temperature dependence of the phase
  * mismatch).  Three calls:
  *

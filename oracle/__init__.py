@@ -26,6 +26,9 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                       sensitivities and full gradients against central
                       finite differences of objective(), with and without
                       a transverse mismatch map
+  spectral_phase      a linear phase Omega m dt is an exact circular shift
+                      by m samples (both signs, 1e-13); a quadratic phase on a
+                      Gaussian gives the chirped-Gaussian closed form (1e-9)
 """
 from __future__ import annotations
 
@@ -256,7 +259,7 @@ def thermal_matrix(nx: int, ny: int, dx: float, dy: float):
     sparse matrix (row index y * nx + x), with T = 0 half a cell outside the
     window: the missing neighbour of an edge point is its mirror image -T, so
     the edge's diagonal entry gains one more 1/d^2.  An axis of length 1 has
-    no derivative along it (Sec. 3, heat equation; the boundary reading is the
+    no derivative along it (Sec. 4.1, heat equation; the boundary reading is the
     crystal's side faces held at the mount temperature)."""
     import scipy.sparse as sp
 

@@ -508,7 +508,7 @@ void orc_spectrum(const orc_problem* pb, const cplx* fields, double* spectrum) {
   free(col);
 }
 
-/* Heat load of the thermal model (Sec. 3, the source term Q of the heat
+/* Heat load of the thermal model (Sec. 4.1, the source term Q of the heat
  * equation): the absorbed optical power density
  *   Q(x, y) = sum_f alpha_f I_f,   I_f = 1/2 c eps0 n_f |A_f|^2,
  * alpha_f the intensity absorption coefficient (the linear step damps the

@@ -1,4 +1,4 @@
-// Thermal model entry points (Sec. 3: the steady-state heat equation
+// Thermal model entry points (Sec. 4.1: the steady-state heat equation
 // lap T = -Q / kappa on the fields' grid, and the temperature-dependent phase
 // mismatch): heat load of the fields, the transverse Poisson solve and the
 // mismatch map it induces.  Kernels in k_thermal.cu.

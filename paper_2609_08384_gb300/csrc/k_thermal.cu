@@ -1,4 +1,4 @@
-// Thermal model (Sec. 3: steady-state heat equation on the fields' grid and the
+// Thermal model (Sec. 4.1: steady-state heat equation on the fields' grid and the
 // temperature dependence of the phase mismatch).
 //
 // heat_load_kernel   Q(x, y) += sum_f c_f sum_tau |A_f|^2: one pass over the

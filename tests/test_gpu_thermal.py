@@ -1,4 +1,4 @@
-"""Thermal model on the GPU against the FP64 oracle (Sec. 3: heat equation on
+"""Thermal model on the GPU against the FP64 oracle (Sec. 4.1: heat equation on
 the fields' grid, temperature-dependent phase mismatch).
 
 Tolerances: the heat load squares FP32 fields (FP32 partial sums of four

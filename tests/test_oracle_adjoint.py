@@ -182,3 +182,55 @@ def test_gradient_under_mismatch_map_matches_differences(three):
         assert abs(gphi[p] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (p, gphi[p], fd)
     _, gphi0, gdk0 = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf)
     assert np.linalg.norm(gdk - gdk0) > 0.1 * np.linalg.norm(gdk)
+
+
+def _centred_omega(nt, dt):
+    """Omega_p = 2 pi (p - NT/2) / (NT dt): the centred order of the spectral-phase vector."""
+    return 2 * np.pi * (np.arange(nt) - nt // 2) / (nt * dt)
+
+
+@pytest.mark.parametrize("nt,shift", [(64, 5), (64, -7), (48, 11), (48, -1), (256, 100)])
+@pytest.mark.parametrize("sign", [+1, -1])
+def test_spectral_phase_linear_phase_is_an_exact_circular_shift(nt, shift, sign):
+    """A linear spectral phase phi(Omega) = Omega m dt multiplies each DFT bin
+    by e^{+2 pi i k m / NT}; the inverse transform then returns the pulse
+    advanced by exactly m samples: out[t] = in[(t + m) mod NT] (sign -1 delays
+    it).  Fixes the sign of phi, the centred index of each bin (an off-by-one
+    turns the shift into a shift times a constant phase and breaks the Nyquist
+    bin) and the 1/NT of the inverse."""
+    dt = 7 * FS
+    g = wl.Grid(4, 3, nt, UM, UM, dt)
+    prob = oracle.make_problem(g, wl.shg_fields(), wl.D_EFF)
+    rng = np.random.default_rng(abs(1000 * nt + 31 * shift) + (sign > 0))
+    a = rng.standard_normal((nt, 3, 4)) + 1j * rng.standard_normal((nt, 3, 4))
+    phi = _centred_omega(nt, dt) * shift * dt
+    out = oracle.spectral_phase(prob, a, phi, sign)
+    want = np.roll(a, -sign * shift, axis=0)
+    assert np.abs(out - want).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("beta_over_tau2", [0.7, -1.3])
+def test_spectral_phase_quadratic_phase_gives_the_chirped_gaussian(beta_over_tau2):
+    """phi(Omega) = beta Omega^2 / 2 on A = exp(-tau^2/tau0^2).  With the
+    forward transform e^{-i Omega tau}, A~(Omega) = sqrt(pi) tau0
+    exp(-Omega^2 tau0^2 / 4); times e^{i beta Omega^2/2} and transformed back,
+    A'(tau) = tau0 / sqrt(tau0^2 - 2 i beta) exp(-tau^2 / (tau0^2 - 2 i beta))
+    (principal root).  The window holds the chirped pulse to e^{-50} and the
+    spectrum to e^{-300}, so the discrete result equals the closed form to
+    rounding.  The sign of beta's imaginary part pins the sign of phi."""
+    nt, dt = 512, 2 * FS
+    tau0 = 12 * dt
+    beta = beta_over_tau2 * tau0**2
+    g = wl.Grid(2, 2, nt, UM, UM, dt)
+    prob = oracle.make_problem(g, wl.shg_fields(), wl.D_EFF)
+    tau = (np.arange(nt) - nt // 2) * dt
+    a = np.broadcast_to(np.exp(-(tau / tau0) ** 2)[:, None, None], (nt, 2, 2)).astype(np.complex128)
+    phi = beta * _centred_omega(nt, dt) ** 2 / 2
+    out = oracle.spectral_phase(prob, a, phi, +1)
+    q = tau0**2 - 2j * beta
+    want = tau0 / np.sqrt(q) * np.exp(-tau**2 / q)
+    assert np.abs(out[:, 1, 0] - want).max() < 1e-9
+    # the conjugate chirp (sign -1) is the closed form with beta -> -beta
+    back = oracle.spectral_phase(prob, a, phi, -1)
+    qm = tau0**2 + 2j * beta
+    assert np.abs(back[:, 0, 1] - tau0 / np.sqrt(qm) * np.exp(-tau**2 / qm)).max() < 1e-9

@@ -1,4 +1,4 @@
-"""Oracle pins for the thermal model (Sec. 3: the steady-state heat equation
+"""Oracle pins for the thermal model (Sec. 4.1: the steady-state heat equation
 lap T = -Q / kappa on the fields' grid; heat load from the absorbed power).
 
 The solve is pinned by what the discrete and continuum problems fix:
