@@ -34,6 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "grid-point·field·z-steps/sec and % of HBM roofline, plain vs batched vs adjoint"
 UNIT = "grid-point·field·z-steps/s"
 KINDS = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
+# bytes the four passes of a z-step read and write per grid point and field (16 each)
+DESIGN_BYTES = 64
 FALLBACK_HBM_GBS = 6800.0
 # FP32 peak derived from the unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA)
 # at the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz, 2070 MHz on this pool)
@@ -432,9 +434,9 @@ def adjoint_form(dev):
     a0 = wl.peak_amplitude(1e13, wl.N_F)
     F = wl.focused_pulse(p.grid, p.fields[1], a0, 50 * wl.UM, 200 * wl.FS, p.length).astype(np.complex64)
     dev_in = [torch.zeros_like(torch.from_numpy(F)).to(dev), torch.from_numpy(F).to(dev)]
-    w = br.shg_efficiency_weights(p.fields, F.astype(np.complex128))
     stream = torch.cuda.Stream(device=dev)
     s = br.Solver(p.grid, p.fields, p.d_eff, 0.0, stream=stream, device=dev)
+    w = s.shg_efficiency_weights(dev_in)
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase)
     s.adjoint_backward(1.0)
@@ -572,10 +574,12 @@ def run_ours(args):
     ms_max = _max_over_ranks(dist, ms, dev)
     value = world * units_per_step * args.steps / (ms_max / 1e3)
 
-    # roofline of the dominant kernel.  HBM view: algorithmic bytes = one read
-    # and one write of every field's state per launch (16 B per grid point per
-    # field).  ALU view: algorithmic FP32 flops per launch against the FP32
-    # peak.  The bound reported is the one the kernel is closer to.
+    # roofline of the dominant kernel.  HBM view (the reported roofline):
+    # algorithmic bytes = one read and one write of every field's state per
+    # launch (16 B per grid point per field) against the measured copy
+    # bandwidth.  ALU view (roofline_other_bound): algorithmic FP32 flops per
+    # launch against the FP32 FMA rate measured on this GPU by the library's
+    # probe (brahms_fp32_fma_rate), the nominal unit-count peak beside it.
     main = int(np.argmax(kind_ms[:4]))
     alg_bytes = 16.0 * g.npoints * problem.nfields
     avg_s = kind_ms[main] / max(1, kind_n[main]) / 1e3
@@ -585,14 +589,18 @@ def run_ours(args):
     roof_hbm = {"bound": "hbm", "kernel": KINDS[main], "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": f"{peak_kind} hbm_gbs (copy)",
                 "alg_bytes_per_launch": alg_bytes}
-    fp_peak, mhz = _fp32_peak_tflops()
+    fp_nominal, mhz = _fp32_peak_tflops()
+    with torch.cuda.stream(stream):
+        fp_peak = br.fp32_fma_rate(stream)
     alg_flops = alg_flops_per_point_field(KINDS[main], problem) * g.npoints * problem.nfields
     roof_alu = {"bound": "alu", "kernel": KINDS[main], "achieved": alg_flops / avg_s / 1e12, "peak": fp_peak,
                 "unit": "TFLOP/s", "frac": alg_flops / avg_s / 1e12 / fp_peak, "traffic": traffic,
-                "peak_source": f"derived: {SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz",
+                "peak_source": "measured: brahms_fp32_fma_rate (16 FMA chains per thread on every SM)",
+                "nominal_peak": fp_nominal,
+                "nominal_source": f"{SMS} SMs x {FP32_LANES} FP32 lanes x 2 flop x {mhz:.0f} MHz",
                 "alg_flops_per_launch": alg_flops}
-    roofline = roof_alu if roof_alu["frac"] > roof_hbm["frac"] else roof_hbm
-    roofline_other = roof_hbm if roofline is roof_alu else roof_alu
+    roofline = roof_hbm
+    roofline_other = roof_alu
     total_k = float(np.sum(kind_ms))
     def _rate(k, per_unit):
         return float(per_unit / (kind_ms[k] / max(1, kind_n[k]) / 1e3)) if k < 4 and kind_n[k] else None
@@ -612,16 +620,32 @@ def run_ours(args):
     e2e_steps = max(1, min(args.steps, 3))
     torch.cuda.synchronize(dev)
     _barrier(dist)
+    ph = {"set_fields_host_ms": 0.0, "propagate_enqueue_host_ms": 0.0, "get_fields_host_ms": 0.0,
+          "propagate_device_ms": 0.0}
+    pe = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e2e_steps)]
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
+    for k in range(e2e_steps):
+        ta = time.perf_counter()
         solver.set_fields(host_in)
+        pe[k][0].record(stream)
+        tb = time.perf_counter()
         solver.propagate(problem.nz, problem.dz)
+        pe[k][1].record(stream)
+        tc = time.perf_counter()
         solver.get_fields(out=host_out)
+        td = time.perf_counter()
+        ph["set_fields_host_ms"] += 1e3 * (tb - ta)
+        ph["propagate_enqueue_host_ms"] += 1e3 * (tc - tb)
+        ph["get_fields_host_ms"] += 1e3 * (td - tc)
     t_e2e = time.perf_counter() - t0
+    for k in range(e2e_steps):
+        ph["propagate_device_ms"] += pe[k][0].elapsed_time(pe[k][1])
+    ph = {key: v / e2e_steps for key, v in ph.items()}
     t_e2e = _max_over_ranks(dist, t_e2e, dev)
     nbytes = g.npoints * problem.nfields * 8
     e2e = {"value": world * units_per_step * e2e_steps / t_e2e, "unit": UNIT,
-           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps}
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": e2e_steps,
+           "phases_ms_per_step": ph}
     def want(name):
         return not args.no_forms and (args.forms is None or name in args.forms.split(","))
 
@@ -654,8 +678,11 @@ def run_ours(args):
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk, "kernels": kernels, "kernel_timing_every": 10,
             "step_hbm": {"alg_GB_per_s": step_alg_gbs, "alg_bytes_per_point_field_step": 16,
-                         "moved_bytes_per_point_field_step_design": 64,
-                         "moved_GB_per_s": 64.0 * value / 1e9, "moved_frac_of_peak": 64.0 * value / 1e9 / peak},
+                         "design_bytes_per_point_field_step": DESIGN_BYTES,
+                         "design_GB_per_s": DESIGN_BYTES * value / 1e9,
+                         "design_frac_of_peak": DESIGN_BYTES * value / 1e9 / peak,
+                         "note": "design bytes: what the pass structure reads and writes by construction "
+                                 "(the ncu DRAM counters of every pass equal them, profiles/); not a measured rate"},
             "forms": forms}
     print(json.dumps(line), flush=True)
     return 0

@@ -167,8 +167,10 @@ brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectru
  * brahms_set_dk_map replaces both terms, brahms_set_dk_map(ctx, NULL)
  * removes them.  If temperature is not NULL, it copies T [K above the
  * mount, ny*nx doubles, x fastest] to it.  kappa_th [W/(m K)] must be > 0, dkdT [1/(m K)] finite.
- * E_STATE if no load was accumulated or set, E_NONFINITE (map not
- * installed) if the load is not finite.  Waits for the stream. */
+ * E_STATE if no load was accumulated or set.  E_NONFINITE if the load or
+ * the temperature is not finite: the thermal map is then not installed and
+ * the map in effect becomes the map of brahms_set_dk_map (none if none).
+ * Waits for the stream. */
 brahms_status brahms_heat_accumulate(brahms_ctx* ctx, double rep_rate, double weight);
 brahms_status brahms_heat_set(brahms_ctx* ctx, const double* q);
 brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, double* temperature);
@@ -200,9 +202,16 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
  * tau-pass of brahms_propagate a persistent kernel that stages tiles of that
  * many x columns through shared memory with double-buffered TMA copies
  * (needs nt in {256, 512} and nx >= 16, else E_SIZE); 0 (the default) keeps
- * the plain tau-pass (and turns the field streams off while set).  E_ARG for an unknown
- * option or value.  brahms_get_option returns the current value or -1. */
-enum { BRAHMS_OPT_TMA_TAU = 1, BRAHMS_OPT_FIELD_STREAMS = 2 };
+ * the plain tau-pass (and turns the field streams off while set).
+ * BRAHMS_OPT_TMA_WAIT_US: the limit, in microseconds (0 .. 2000000, default
+ * 2000000 = 2 s), of each wait of the TMA tau-pass for a tile's copy.  When a
+ * wait runs out the kernel lets its copies in flight land (waiting at most
+ * 2 s more), leaves its remaining tiles untransformed and returns; the next
+ * synchronising call reports E_TIMEOUT and the fields must be set again.
+ * (A short limit makes the waits run out on purpose: the way to test that
+ * error path without hanging the GPU.)  E_ARG for an unknown option or
+ * value.  brahms_get_option returns the current value or -1. */
+enum { BRAHMS_OPT_TMA_TAU = 1, BRAHMS_OPT_FIELD_STREAMS = 2, BRAHMS_OPT_TMA_WAIT_US = 3 };
 brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value);
 int brahms_get_option(const brahms_ctx* ctx, int option);
 
@@ -239,9 +248,23 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
 
 /* Reverse sweep for the last brahms_adjoint_forward: writes gscale * dJ/dphi
  * (nt entries, centred order; zeros if no phase was applied) and
- * gscale * dJ/d dk_j (nz entries); either pointer may be NULL.  Leaves the
- * context state undefined (call brahms_set_fields before propagating). */
+ * gscale * dJ/d dk_j (nz entries); either pointer may be NULL.  May be called
+ * again for the same forward (another gscale).  E_STATE if the last
+ * brahms_adjoint_forward failed or never ran, or if any call changed the
+ * fields, the mismatch map or the profile since it returned
+ * (brahms_set_fields, brahms_propagate, brahms_transform, brahms_set_dk_map,
+ * brahms_set_dk_profile, brahms_thermal_map): the reverse sweep reads the
+ * forward's final fields and map, so it runs only on those. */
 brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* grad_phi, double* grad_dk);
+
+/* Weights that make J of brahms_adjoint_forward the SHG efficiency
+ * eta = E_SH(L) / E_F(0) of the current two fields (SH, F), as set by
+ * brahms_set_fields with the input: w_SH = n_SH / (n_F sum |A_F|^2),
+ * w_F = 0 (the common factor 1/2 c eps0 dx dy dtau of both energies cancels;
+ * a spectral phase on F keeps E_F(0)).  FP64 sum on the device; waits.
+ * weights: 2 doubles.  E_ARG for three fields or a zero fundamental,
+ * E_STATE without fields. */
+brahms_status brahms_shg_efficiency_weights(brahms_ctx* ctx, double* weights);
 
 /* ------------------------------------------------------------------------
  * Batched form (two-field SHG sweeps): many independent simulations of
@@ -291,8 +314,17 @@ brahms_status brahms_batch_get_schedule(const brahms_batch* b, int shape, int* g
 brahms_status brahms_batch_run(brahms_batch* b);
 
 /* Wait for the stream; E_TIMEOUT if the persistent kernel gave up waiting
- * for a pass of some instance (its bounded waits expired). */
+ * for a pass of some instance (its bounded waits expired).  The instances'
+ * fields are then partly advanced: set them again before the next run. */
 brahms_status brahms_batch_sync(brahms_batch* b);
+
+/* Limit [s] of each bounded wait of the persistent kernel (a CTA waiting for
+ * runnable work or for the previous pass of an instance), 0 .. 3600;
+ * default 5.  On expiry the kernel records E_TIMEOUT (reported by
+ * brahms_batch_sync) and every CTA returns.  (A zero limit makes the waits
+ * run out on purpose: the way to test that error path without hanging the
+ * GPU.)  Takes effect at the next brahms_batch_run.  E_ARG out of range. */
+brahms_status brahms_batch_set_timeout(brahms_batch* b, double seconds);
 
 /* Copy instance `index`'s envelopes out (2 pointers, complex64); waits. */
 brahms_status brahms_batch_get_fields(brahms_batch* b, int index, void* const* out, int dtype, int on_device);
@@ -325,12 +357,32 @@ const char* brahms_batch_last_error(const brahms_batch* b);
  * carries over, but all calls share that array: calls whose work overlaps on
  * the GPU (other streams, other threads) race and must be serialised by the
  * caller.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Returns E_ARG for NULL pointers or
+ * (cudaGetSymbolAddress) with that device current, and so does the first
+ * call after a cudaDeviceReset has replaced the device's context (the array
+ * then lives at a new address); make those calls before any stream capture.  Returns E_ARG for NULL pointers or
  * non-positive spacings, E_CUDA if a launch fails; asynchronous otherwise. */
 brahms_status brahms_energy_static(const void* const* fields, int nfields, int nx, int ny, int nt, double dx,
                                    double dy, double dt, const brahms_field_params* fp, double* energy_j_dev,
                                    void* cuda_stream);
+
+/* Measured FP32 fused multiply-add rate of the current GPU [TFLOP/s, 2 flops
+ * per FMA]: the peak that the ALU view of a kernel's roofline divides by.
+ * (The paper has no counterpart; the target's roofline is HBM bandwidth, and
+ * the FFT and RK4 passes are also bounded by FP32 issue, whose peak no
+ * published figure gives for this GPU.)  Runs about 0.1 s of independent FMA
+ * chains on every SM on cuda_stream, timed with CUDA events after a warm-up
+ * launch; waits.  E_ARG for a NULL output, E_CUDA if a launch fails. */
+brahms_status brahms_fp32_fma_rate(void* cuda_stream, double* tflops);
+
+/* Fault injection for tests of the error paths: the next `count` device or
+ * pinned-host allocations the library makes (context workspace and its
+ * pinned readback word, adjoint checkpoints, thermal buffers, batch memory)
+ * report failure (the calls return BRAHMS_E_OOM) without calling the CUDA
+ * allocator; count 0 clears it.  Process-wide and thread-safe.  E_ARG for a
+ * negative count.  brahms_pending_allocation_failures returns how many of
+ * them have not been consumed yet. */
+brahms_status brahms_fail_next_allocations(int count);
+int brahms_pending_allocation_failures(void);
 
 /* Release the context and any memory the library allocated for it. */
 void brahms_free(brahms_ctx* ctx);

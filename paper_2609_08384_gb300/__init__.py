@@ -32,6 +32,7 @@ BRAHMS_C128 = 1
 KIND_NAMES = ("xpass_nl", "ypass_fwd", "tpass_prop", "ypass_inv", "other")
 BRAHMS_OPT_TMA_TAU = 1
 BRAHMS_OPT_FIELD_STREAMS = 2
+BRAHMS_OPT_TMA_WAIT_US = 3
 
 # Every entry point declared in include/brahms.h, with its ctypes signature.
 _c = ctypes
@@ -72,6 +73,7 @@ SIGNATURES = {
     "brahms_adjoint_forward": (_c.c_int, [_vp, _c.POINTER(_vp), _c.c_int, _c.c_int, _dp, _c.c_int, _dp, _c.c_int,
                                           _c.c_double, _dp, _c.c_int, _dp]),
     "brahms_adjoint_backward": (_c.c_int, [_vp, _c.c_double, _dp, _dp]),
+    "brahms_shg_efficiency_weights": (_c.c_int, [_vp, _dp]),
     "brahms_batch_create": (_c.c_int, [_c.POINTER(_vp), _vp]),
     "brahms_batch_add": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_double, _c.c_double, _c.c_double,
                                     _c.POINTER(FieldParams), _c.c_double, _c.c_double, _c.c_int, _c.c_double,
@@ -83,11 +85,15 @@ SIGNATURES = {
                                              _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "brahms_batch_run": (_c.c_int, [_vp]),
     "brahms_batch_sync": (_c.c_int, [_vp]),
+    "brahms_batch_set_timeout": (_c.c_int, [_vp, _c.c_double]),
     "brahms_batch_get_fields": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_vp), _c.c_int, _c.c_int]),
     "brahms_batch_info": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
                                      _llp]),
     "brahms_batch_free": (None, [_vp]),
     "brahms_batch_last_error": (_c.c_char_p, [_vp]),
+    "brahms_fp32_fma_rate": (_c.c_int, [_vp, _dp]),
+    "brahms_fail_next_allocations": (_c.c_int, [_c.c_int]),
+    "brahms_pending_allocation_failures": (_c.c_int, []),
     "brahms_free": (None, [_vp]),
     "brahms_last_error": (_c.c_char_p, [_vp]),
     "brahms_status_string": (_c.c_char_p, [_c.c_int]),
@@ -297,16 +303,27 @@ class Solver:
         w = np.ascontiguousarray(weights, dtype=np.float64)
         ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
         J = ctypes.c_double()
+        # recorded first: after a failed forward the C library answers a
+        # backward with BRAHMS_E_STATE
+        self._adj = (int(nz), ph is not None)
         _check(self.ctx, load().brahms_adjoint_forward(
             self.ctx, _ptr_array(ptrs), dtype, int(dev), None if ph is None else ph.ctypes.data_as(_dp),
             int(phi_field), dks.ctypes.data_as(_dp), int(nz), float(dz), w.ctypes.data_as(_dp),
             int(checkpoint_interval), ctypes.byref(J)))
-        self._adj = (int(nz), ph is not None)
         return J.value
+
+    def shg_efficiency_weights(self, fields=None):
+        """Weights (w_SH, w_F) that make adjoint_forward's J the SHG efficiency
+        of the input; ``fields`` (if given) are set first as the input."""
+        if fields is not None:
+            self.set_fields(fields)
+        w = np.zeros(2)
+        _check(self.ctx, load().brahms_shg_efficiency_weights(self.ctx, w.ctypes.data_as(_dp)))
+        return w
 
     def adjoint_backward(self, gscale=1.0):
         """(gscale dJ/dphi or None, gscale dJ/d dk) for the last adjoint_forward."""
-        nz, has_phi = self._adj
+        nz, has_phi = getattr(self, "_adj", (1, False))
         gphi = np.zeros(self.grid.nt)
         gdk = np.zeros(nz)
         _check(self.ctx, load().brahms_adjoint_backward(self.ctx, float(gscale), gphi.ctypes.data_as(_dp),
@@ -417,6 +434,10 @@ class Batch:
     def sync(self):
         self._chk(load().brahms_batch_sync(self.h))
 
+    def set_timeout(self, seconds: float):
+        """Limit of each bounded wait of the persistent kernel (default 5 s)."""
+        self._chk(load().brahms_batch_set_timeout(self.h, float(seconds)))
+
     def get_fields(self, index, on_device=False):
         import torch
 
@@ -450,12 +471,24 @@ class Batch:
             pass
 
 
-def shg_efficiency_weights(fields, input_f):
-    """Weights that make J the SHG efficiency E_SH(L)/E_F(0) for fields
-    (SH, F): w_SH = n_SH / (n_F sum |A_F(0)|^2), w_F = 0 (the common factor
-    1/2 c eps0 dx dy dtau cancels; the spectral phase keeps E_F(0))."""
-    s = float(np.sum(np.abs(np.asarray(input_f, dtype=np.complex128)) ** 2))
-    return np.array([fields[0].n / (fields[1].n * s), 0.0])
+def fp32_fma_rate(stream=None) -> float:
+    """Measured FP32 FMA rate of the current GPU in TFLOP/s."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(None, load().brahms_fp32_fma_rate(_vp(st.cuda_stream), ctypes.byref(v)))
+    return v.value
+
+
+def fail_next_allocations(count: int) -> None:
+    """Fault injection for tests: the library's next ``count`` allocations
+    report failure (BRAHMS_E_OOM); 0 clears it."""
+    _check(None, load().brahms_fail_next_allocations(int(count)))
+
+
+def pending_allocation_failures() -> int:
+    return int(load().brahms_pending_allocation_failures())
 
 
 def shg_efficiency_function():

@@ -94,7 +94,7 @@ brahms_status adj_alloc(brahms_ctx* ctx, int nz, int K, int nseg) {
     if (ctx->adj_mem) cudaFree(ctx->adj_mem);
     ctx->adj_mem = nullptr;
     ctx->adj_bytes = 0;
-    if (cudaMalloc((void**)&ctx->adj_mem, off) != cudaSuccess) {
+    if (brahms::dev_alloc((void**)&ctx->adj_mem, off) != cudaSuccess) {
       cudaGetLastError();
       return fail(ctx, BRAHMS_E_OOM, "adjoint checkpoint memory");
     }
@@ -121,6 +121,8 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
                                      const double* phi, int phi_field, const double* dk, int nz, double dz,
                                      const double* weights, int checkpoint_interval, double* J) {
   if (!ctx) return BRAHMS_E_ARG;
+  // any failure below leaves no forward for brahms_adjoint_backward to reverse
+  ctx->adj_ready = false;
   if (ctx->ny < 2 || ctx->nt < 2) return fail(ctx, BRAHMS_E_SIZE, "the adjoint needs ny >= 2 and nt >= 2");
   if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
     return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
@@ -202,13 +204,16 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
   double j = 0.0;
   for (int f = 0; f < ctx->nf; ++f) j += weights[f] * ctx->energy_host[f];
   if (J) *J = j;
+  ctx->adj_gen = ctx->gen;
   ctx->adj_ready = true;
   return BRAHMS_OK;
 }
 
 brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* grad_phi, double* grad_dk) {
   if (!ctx) return BRAHMS_E_ARG;
-  if (!ctx->adj_ready) return fail(ctx, BRAHMS_E_STATE, "adjoint_backward before adjoint_forward");
+  if (!ctx->adj_ready) return fail(ctx, BRAHMS_E_STATE, "adjoint_backward without a completed adjoint_forward");
+  if (ctx->adj_gen != ctx->gen)
+    return fail(ctx, BRAHMS_E_STATE, "the fields, map or profile changed after adjoint_forward");
   if (!std::isfinite(gscale)) return fail(ctx, BRAHMS_E_ARG, "gscale is not finite");
   const int nz = ctx->adj_nz, K = ctx->adj_K, nseg = ctx->adj_nseg, nf = ctx->nf, nx = ctx->nx;
   const double dz = ctx->adj_dz;

@@ -83,7 +83,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
     ctx->ws = (char*)workspace;
   } else {
     void* p = nullptr;
-    if (cudaMalloc(&p, ctx->L.total) != cudaSuccess) {
+    if (brahms::dev_alloc(&p, ctx->L.total) != cudaSuccess) {
       cudaGetLastError();
       delete ctx;
       return BRAHMS_E_OOM;
@@ -91,7 +91,7 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
     ctx->ws = (char*)p;
     ctx->own_ws = true;
   }
-  if (cudaMallocHost((void**)&ctx->energy_host, sizeof(double) * 4) != cudaSuccess) {
+  if (brahms::pinned_alloc((void**)&ctx->energy_host, sizeof(double) * 4) != cudaSuccess) {
     cudaGetLastError();
     brahms_free(ctx);
     return BRAHMS_E_OOM;
@@ -172,6 +172,7 @@ brahms_status brahms_set_fields(brahms_ctx* ctx, const void* const* fields, int 
   ctx->phi = 0.0;
   ctx->step = 0;
   ctx->have_fields = true;
+  touch(ctx);
   brahms_status s = finish_with_check(ctx);
   if (s == BRAHMS_E_NONFINITE) {
     ctx->have_fields = false;
@@ -186,6 +187,7 @@ brahms_status brahms_set_dk_profile(brahms_ctx* ctx, const double* dk, int n) {
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(dk[i])) return fail(ctx, BRAHMS_E_ARG, "profile has non-finite entries");
   ctx->dk_profile.assign(dk, dk + n);
+  touch(ctx);
   return BRAHMS_OK;
 }
 
@@ -194,6 +196,7 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
   if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "propagate before set_fields");
   if (nz < 0 || !(dz > 0) || !std::isfinite(dz)) return fail(ctx, BRAHMS_E_ARG, "need nz >= 0 and dz > 0");
   if (nz == 0) return BRAHMS_OK;
+  touch(ctx);
   brahms_status s = build_tables(ctx, dz);
   if (s != BRAHMS_OK) return s;
   const int nx = ctx->nx, ny = ctx->ny, nt = ctx->nt, nf = ctx->nf;
@@ -224,7 +227,8 @@ brahms_status brahms_propagate(brahms_ctx* ctx, int nz, double dz) {
         BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_prop_pointwise(at, nf, ctx->stream); }));
       else if (ctx->use_tma)
         BR_CK(launch(ctx, 2, 1, [&] {
-          return brahms::run_tpass_prop_tma(nt, ctx->use_tma, ctx->tmap_state, at, ctx->dev_err, ctx->stream);
+          return brahms::run_tpass_prop_tma(nt, ctx->use_tma, ctx->tmap_state, at, ctx->dev_err, ctx->tma_wait_ns,
+                                            ctx->stream);
         }));
       else
         BR_CK(launch(ctx, 2, 1, [&] { return brahms::run_tpass_prop(nt, at, ctx->stream); }));
@@ -291,6 +295,21 @@ brahms_status brahms_energy(brahms_ctx* ctx, double* energy_j, double* photons) 
   return s;
 }
 
+brahms_status brahms_shg_efficiency_weights(brahms_ctx* ctx, double* weights) {
+  if (!ctx) return BRAHMS_E_ARG;
+  if (!weights) return fail(ctx, BRAHMS_E_ARG, "weights is NULL");
+  if (ctx->nf != 2) return fail(ctx, BRAHMS_E_ARG, "SHG efficiency weights need the two fields (SH, F)");
+  if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "no fields set");
+  const brahms_status s = finish_with_check(ctx);  // energy_host[f] = sum |A_f|^2
+  if (s != BRAHMS_OK) return s;
+  const double sum_f = ctx->energy_host[1];
+  if (!(sum_f > 0.0)) return fail(ctx, BRAHMS_E_ARG, "the fundamental is zero");
+  // eta = E_SH(L) / E_F(0): E = 1/2 c eps0 n sum |A|^2 dx dy dtau, the common factors cancel
+  weights[0] = ctx->fp[0].n / (ctx->fp[1].n * sum_f);
+  weights[1] = 0.0;
+  return BRAHMS_OK;
+}
+
 brahms_status brahms_sync(brahms_ctx* ctx) {
   if (!ctx) return BRAHMS_E_ARG;
   if (!ctx->have_fields) {
@@ -304,6 +323,7 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   if (!ctx) return BRAHMS_E_ARG;
   if (!ctx->have_fields) return fail(ctx, BRAHMS_E_STATE, "no fields set");
   if (direction != -1 && direction != 1) return fail(ctx, BRAHMS_E_ARG, "direction must be -1 or +1");
+  touch(ctx);
   const brahms::AxisArgs ay = aargs(ctx, 1), at = aargs(ctx, 2, false);
   const bool inv = direction == 1;
   brahms::XPassArgs a = xargs(ctx, inv ? brahms::XM_INV : brahms::XM_FWD, 1.0);
@@ -320,6 +340,7 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
   if (!dk_map) {
     ctx->have_map = false;
     ctx->have_user_map = false;
+    touch(ctx);
     return BRAHMS_OK;
   }
   const size_t n = (size_t)ctx->nx * ctx->ny;
@@ -330,6 +351,7 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
   BR_CK(cudaStreamSynchronize(ctx->stream));
   ctx->have_map = true;
   ctx->have_user_map = true;
+  touch(ctx);
   return BRAHMS_OK;
 }
 
@@ -413,6 +435,11 @@ brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value) {
     ctx->field_streams = value;
     return BRAHMS_OK;
   }
+  if (option == BRAHMS_OPT_TMA_WAIT_US) {
+    if (value < 0 || value > 2000000) return fail(ctx, BRAHMS_E_ARG, "TMA wait limit: 0 to 2000000 us");
+    ctx->tma_wait_ns = 1000ULL * (unsigned long long)value;
+    return BRAHMS_OK;
+  }
   return fail(ctx, BRAHMS_E_ARG, "unknown option");
 }
 
@@ -420,6 +447,7 @@ int brahms_get_option(const brahms_ctx* ctx, int option) {
   if (!ctx) return -1;
   if (option == BRAHMS_OPT_TMA_TAU) return ctx->use_tma;
   if (option == BRAHMS_OPT_FIELD_STREAMS) return ctx->field_streams;
+  if (option == BRAHMS_OPT_TMA_WAIT_US) return (int)(ctx->tma_wait_ns / 1000ULL);
   return -1;
 }
 

@@ -24,6 +24,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "brahms.h"
 #include "kernels.cuh"
 
@@ -416,6 +417,15 @@ brahms_status bfail(brahms_batch* b, brahms_status s, const std::string& m) {
     if (e_ != cudaSuccess) return bfail(b, BRAHMS_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// an allocation that failed is BRAHMS_E_OOM (the batch stays usable)
+#define BB_ALLOC(call)                                                      \
+  do {                                                                      \
+    if ((call) != cudaSuccess) {                                            \
+      cudaGetLastError();                                                   \
+      return bfail(b, BRAHMS_E_OOM, std::string(#call) + ": out of memory"); \
+    }                                                                       \
+  } while (0)
+
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
 void free_device(brahms_batch* b) {
@@ -487,9 +497,9 @@ brahms_status prepare(brahms_batch* b) {
     off += 1 + 4LL * d.nz;
   }
   b->done_count = (size_t)off;
-  BB_CK(cudaMalloc(&b->d_inst, sizeof(InstDev) * n));
-  BB_CK(cudaMalloc(&b->d_next, sizeof(unsigned long long) * n));
-  BB_CK(cudaMalloc(&b->d_done, al256(sizeof(unsigned int) * b->done_count) + 256));
+  BB_ALLOC(dev_alloc((void**)&b->d_inst, sizeof(InstDev) * n));
+  BB_ALLOC(dev_alloc((void**)&b->d_next, sizeof(unsigned long long) * n));
+  BB_ALLOC(dev_alloc((void**)&b->d_done, al256(sizeof(unsigned int) * b->done_count) + 256));
   b->d_status = reinterpret_cast<int*>(reinterpret_cast<char*>(b->d_done) + al256(sizeof(unsigned int) * b->done_count));
   BB_CK(cudaMemcpy(b->d_inst, h.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
   // launch shape: all CTAs co-resident
@@ -576,7 +586,7 @@ brahms_status brahms_batch_create(brahms_batch** out, void* cuda_stream) {
   b->stream = (cudaStream_t)cuda_stream;
   for (int s = 0; s < kNumShapes; ++s)
     for (int k = 0; k < 3; ++k) b->gran[s][k] = 1;
-  if (cudaMallocHost((void**)&b->h_status, sizeof(int)) != cudaSuccess) {
+  if (pinned_alloc((void**)&b->h_status, sizeof(int)) != cudaSuccess) {
     delete b;
     return BRAHMS_E_OOM;
   }
@@ -624,7 +634,7 @@ brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double d
          o_twt = o_twx + al256(sizeof(float4) * tw_table_size_of(nx)),
          o_px = o_twt + al256(sizeof(float4) * tw_table_size_of(nt)), o_py = o_px + al256(sizeof(float2) * 2 * nx),
          o_pt = o_py + al256(sizeof(float2) * 2 * ny), total = o_pt + al256(sizeof(float2) * 2 * nt);
-  if (cudaMalloc((void**)&I.mem, total) != cudaSuccess) {
+  if (dev_alloc((void**)&I.mem, total) != cudaSuccess) {
     cudaGetLastError();
     return bfail(b, BRAHMS_E_OOM, "device allocation failed");
   }
@@ -670,6 +680,14 @@ brahms_status brahms_batch_set_granularity(brahms_batch* b, int shape, int gx, i
   b->gran[shape][1] = gy;
   b->gran[shape][2] = gt;
   b->dirty = true;
+  return BRAHMS_OK;
+}
+
+brahms_status brahms_batch_set_timeout(brahms_batch* b, double seconds) {
+  if (!b) return BRAHMS_E_ARG;
+  if (!(seconds >= 0.0) || !(seconds <= 3600.0)) return bfail(b, BRAHMS_E_ARG, "timeout must be in [0, 3600] s");
+  b->timeout_s = seconds;
+  b->dirty = true;  // the limit is an argument of the captured launch
   return BRAHMS_OK;
 }
 
@@ -728,7 +746,7 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
   size_t bytes = 0;
   for (auto& I : b->inst) bytes += sizeof(float2) * 2 * (size_t)I.npoints();
   char* save = nullptr;
-  BB_CK(cudaMalloc(&save, bytes));
+  BB_ALLOC(dev_alloc((void**)&save, bytes));
   auto copy_all = [&](bool to_save) -> cudaError_t {
     size_t o = 0;
     for (auto& I : b->inst) {

@@ -25,7 +25,7 @@ brahms_status thermal_alloc(brahms_ctx* ctx) {
   const size_t o_h = take(sizeof(double) * nxy), o_t = take(sizeof(double) * nxy);
   const size_t o_x = take(sizeof(double2) * ctx->nx), o_y = take(sizeof(double2) * ctx->ny);
   const size_t o_b = take(sizeof(int));
-  if (cudaMalloc((void**)&ctx->th_mem, off) != cudaSuccess) {
+  if (brahms::dev_alloc((void**)&ctx->th_mem, off) != cudaSuccess) {
     cudaGetLastError();
     ctx->th_mem = nullptr;
     return fail(ctx, BRAHMS_E_OOM, "thermal model memory");
@@ -118,9 +118,16 @@ brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, 
     BR_CK(cudaMemcpyAsync(temperature, ctx->th_temp, sizeof(double) * ctx->nx * ctx->ny, cudaMemcpyDeviceToHost,
                           ctx->stream));
   BR_CK(cudaStreamSynchronize(ctx->stream));
+  touch(ctx);
   if (bad) {
-    ctx->have_map = false;
-    return fail(ctx, BRAHMS_E_NONFINITE, "heat load or temperature not finite; map not installed");
+    // the solve wrote the map in place: put back the map of brahms_set_dk_map
+    // (or none), so that propagation goes on under the map the caller set
+    if (ctx->have_user_map)
+      BR_CK(cudaMemcpyAsync(ctx->dkmap_dev, ctx->usermap_dev, sizeof(double) * ctx->nx * ctx->ny,
+                            cudaMemcpyDeviceToDevice, ctx->stream));
+    BR_CK(cudaStreamSynchronize(ctx->stream));
+    ctx->have_map = ctx->have_user_map;
+    return fail(ctx, BRAHMS_E_NONFINITE, "heat load or temperature not finite; the map of brahms_set_dk_map stays");
   }
   ctx->have_map = true;
   return BRAHMS_OK;

@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "alloc_hook.h"
 #include "brahms.h"
 #include "kernels.cuh"
 
@@ -81,6 +82,7 @@ struct brahms_ctx {
   bool have_map = false;
   bool have_user_map = false;
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
+  unsigned long long tma_wait_ns = 2000000000ULL;  // limit of each TMA tile wait (BRAHMS_OPT_TMA_WAIT_US)
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
   int use_tma = 0;  // 0 plain tau-pass; 16 or 8: TMA tau-pass with tiles of that many columns
   // per-field streams for the y/tau/y chain of a step (created on first use)
@@ -89,6 +91,10 @@ struct brahms_ctx {
   cudaEvent_t ev_x = nullptr, ev_y[3] = {nullptr, nullptr, nullptr}, ev_done[3] = {nullptr, nullptr, nullptr};
   double tab_dz = NAN;
   bool have_fields = false;
+  // generation of the state: every call that changes the fields, the map or
+  // the profile advances it; the adjoint's reverse sweep runs only for the
+  // generation its forward left
+  unsigned long long gen = 0;
   double z = 0.0, phi = 0.0;
   long long step = 0;
   std::vector<double> dk_profile;
@@ -118,6 +124,7 @@ struct brahms_ctx {
   int adj_nz = 0, adj_K = 0, adj_nseg = 0, adj_phi_field = -1;
   double adj_dz = 0.0;
   bool adj_ready = false;
+  unsigned long long adj_gen = 0;  // gen at the end of the last brahms_adjoint_forward
   bool adj_store_all = false;  // the forward recorded every step (no recomputation)
   std::vector<double> adj_weights, adj_dk, adj_phis;
   // thermal model (allocated on first use)
@@ -138,6 +145,9 @@ inline brahms_status fail(brahms_ctx* c, brahms_status s, const std::string& msg
   if (c) c->err = msg;
   return s;
 }
+
+// the state, the map or the profile changed
+inline void touch(brahms_ctx* c) { ++c->gen; }
 
 inline brahms_status cuda_fail(brahms_ctx* c, cudaError_t e, const char* where) {
   std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "brahms.h"
@@ -28,20 +29,55 @@ static __device__ __align__(256) double g_energy_scratch[kStaticFields * kStatic
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // context the address belongs to (0: unknown)
 
-// Device address of g_energy_scratch on the current device, looked up once
-// per device (the name is only a host-side handle).
+// Identity of the calling thread's current CUDA context, through the driver
+// entry points (no link against libcuda); false if none is current yet or
+// the entry points are missing.
+bool current_context_id(unsigned long long* id) {
+  typedef CUresult (*GetCurrentFn)(CUcontext*);
+  typedef CUresult (*GetIdFn)(CUcontext, unsigned long long*);
+  static GetCurrentFn get_current = nullptr;
+  static GetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetIdFn>(p);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_energy_scratch on the current device (the name is only
+// a host-side handle).  It is looked up once per device, and again when the
+// device's context is not the one the address was taken in: a
+// cudaDeviceReset destroys the context and the library's module with it, and
+// the module loads at a new address in the next context.
 cudaError_t scratch_address(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  unsigned long long id = 0;
+  bool have_id = current_context_id(&id);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || !have_id || g_scratch_ctx[dev] != id) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_energy_scratch);
     if (e != cudaSuccess) return e;
+    if (!have_id) have_id = current_context_id(&id);  // the lookup made the device's context current
     g_scratch_ptr[dev] = static_cast<double*>(p);
+    g_scratch_ctx[dev] = have_id ? id : 0;
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;

@@ -3,16 +3,9 @@
 #include <vector>
 
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
-
-template <class K>
-static cudaError_t set_smem(K kernel, size_t smem, bool& configured) {
-  if (configured) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) configured = true;
-  return e;
-}
 
 template <int N, bool INV, int AXIS>
 static cudaError_t launch_axis(const AxisArgs& a, cudaStream_t s) {
@@ -20,8 +13,8 @@ static cudaError_t launch_axis(const AxisArgs& a, cudaStream_t s) {
   constexpr int TPC = tiles_per_cta<PL>();
   constexpr int THREADS = TPC * tile_threads<PL>();
   const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
-  static bool configured = false;
-  cudaError_t e = set_smem(axis_fft_kernel<PL, INV, AXIS>, smem, configured);
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(axis_fft_kernel<PL, INV, AXIS>, smem, once);
   if (e != cudaSuccess) return e;
   const long long grid = (a.ntiles + TPC - 1) / TPC;
   if (grid <= 0) return cudaSuccess;
@@ -35,8 +28,8 @@ static cudaError_t launch_tprop(const AxisArgs& a, cudaStream_t s) {
   constexpr int TPC = tiles_per_cta<PL>();
   constexpr int THREADS = TPC * tile_threads<PL>();
   const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
-  static bool configured = false;
-  cudaError_t e = set_smem(tpass_prop_kernel<PL>, smem, configured);
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(tpass_prop_kernel<PL>, smem, once);
   if (e != cudaSuccess) return e;
   const long long grid = (a.ntiles + TPC - 1) / TPC;
   if (grid <= 0) return cudaSuccess;

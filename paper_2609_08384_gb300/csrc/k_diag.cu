@@ -2,6 +2,7 @@
 // spectrum over Omega (the Sec. 6 power formula resolved in tau or Omega).
 // Neither kernel writes the state.
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
 
@@ -142,13 +143,9 @@ static cudaError_t launch_spectrum(const AxisArgs& a, double* out, cudaStream_t 
   constexpr int TPC = tiles_per_cta<PL>();
   constexpr int THREADS = TPC * tile_threads<PL>();
   const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(tau_spectrum_kernel<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(tau_spectrum_kernel<PL>, smem, once);
+  if (e != cudaSuccess) return e;
   const long long ctiles = (a.ntiles + TPC - 1) / TPC;
   if (ctiles <= 0) return cudaSuccess;
   const long long grid = ctiles < 2 * 152 ? ctiles : 2 * 152;

@@ -16,6 +16,7 @@
 //                    in-place Stockham FFT, radix 2 and 3, with one barrier
 //                    between the reads and the writes of every stage.
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
 
@@ -284,13 +285,9 @@ cudaError_t sine_lines(double* d, const double2* tw, int n, long long elem, long
   a.elem = elem;
   a.pitch = pitch;
   const size_t smem = sizeof(double2) * 2 * (size_t)n;
-  static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(sine_lines_kernel<SYNTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)std::max<size_t>(smem, 48 * 1024));
-    if (e != cudaSuccess) return e;
-    configured = std::max<size_t>(smem, 48 * 1024);
-  }
+  static SmemMax limit;
+  cudaError_t e = raise_smem_limit_to(sine_lines_kernel<SYNTH>, std::max<size_t>(smem, 48 * 1024), limit);
+  if (e != cudaSuccess) return e;
   sine_lines_kernel<SYNTH><<<lines, kSineThreads, smem, s>>>(a);
   return cudaPeekAtLastError();
 }

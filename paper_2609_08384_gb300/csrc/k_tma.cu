@@ -9,12 +9,15 @@
 // for NT = 512), written to shared memory tau-major with the 16 columns
 // contiguous -- exactly the column-exchange layout of the FFT, so the tile is
 // transformed in place.  Results are stored from registers with coalesced
-// 128-byte rows.  Every mbarrier wait is bounded by %globaltimer; on expiry
-// the kernel records an error flag, waits (bounded) for its copies in flight
-// and returns.
+// 128-byte rows.  Every mbarrier wait is bounded by %globaltimer (the limit
+// is an argument, 2 s by default); on expiry the kernel records an error
+// flag, waits for its copies in flight (bounded by 2 s, whatever the limit,
+// so that no copy can land in shared memory after the CTA has left) and
+// returns.
 #include <cuda.h>
 
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
 
@@ -44,7 +47,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
   return true;
 }
 
-constexpr unsigned long long kTmaWaitNs = 2000000000ULL;  // 2 s
+constexpr unsigned long long kTmaDrainNs = 2000000000ULL;  // 2 s
 
 }  // namespace
 
@@ -57,7 +60,7 @@ __host__ __device__ constexpr size_t tma_smem_bytes() {
 
 template <class PL, int TX>
 __global__ void __launch_bounds__(PL::T * TX, PL::T * TX <= 256 ? 2 : 1)
-    tpass_tma_kernel(const __grid_constant__ CUtensorMap tm, const AxisArgs p, int* err) {
+    tpass_tma_kernel(const __grid_constant__ CUtensorMap tm, const AxisArgs p, int* err, unsigned long long wait_ns) {
   constexpr int N = PL::N, E = PL::E, T = PL::T;
   constexpr int BOX = tma_box_t<PL>();
   constexpr int NBOX = N / BOX;
@@ -117,13 +120,13 @@ __global__ void __launch_bounds__(PL::T * TX, PL::T * TX <= 256 ? 2 : 1)
     const long long next = tile + gridDim.x;
     const bool pending_next = next < ntiles;
     if (threadIdx.x == 0 && pending_next) issue(next, b ^ 1);
-    const bool ok = mbar_wait(smem_u32(&bars[b]), phase[b], kTmaWaitNs);
+    const bool ok = mbar_wait(smem_u32(&bars[b]), phase[b], wait_ns);
     if (__syncthreads_or(!ok)) {
       if (threadIdx.x == 0) {
         atomicExch(err, 1);
         // let the copies in flight land (bounded) before the CTA exits
-        mbar_wait(smem_u32(&bars[b]), phase[b], kTmaWaitNs);
-        if (pending_next) mbar_wait(smem_u32(&bars[b ^ 1]), phase[b ^ 1], kTmaWaitNs);
+        mbar_wait(smem_u32(&bars[b]), phase[b], kTmaDrainNs);
+        if (pending_next) mbar_wait(smem_u32(&bars[b ^ 1]), phase[b ^ 1], kTmaDrainNs);
       }
       break;
     }
@@ -215,23 +218,21 @@ cudaError_t make_tau_tensor_map(void* map128, const float2* data, int nx, int ny
 }
 
 template <class PL, int TX>
-static cudaError_t launch_tma(const void* map128, const AxisArgs& a0, int* err, cudaStream_t s) {
+static cudaError_t launch_tma(const void* map128, const AxisArgs& a0, int* err, unsigned long long wait_ns,
+                              cudaStream_t s) {
   const size_t smem = tma_smem_bytes<PL, TX>();
-  static bool configured = false;
-  static int per_sm = 0, sms = 0;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(tpass_tma_kernel<PL, TX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tpass_tma_kernel<PL, TX>, PL::T * TX, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    configured = true;
-  }
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(tpass_tma_kernel<PL, TX>, smem, once);
+  if (e != cudaSuccess) return e;
+  // resident CTAs on the current device (asked at every launch: a few
+  // microseconds against a launch of about half a millisecond)
+  int dev = 0, per_sm = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tpass_tma_kernel<PL, TX>, PL::T * TX, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
   AxisArgs a = a0;  // tiles of TX columns
   a.xtiles = (a.nx + TX - 1) / TX;
   a.ntiles = a0.ntiles / a0.xtiles * a.xtiles;
@@ -240,21 +241,22 @@ static cudaError_t launch_tma(const void* map128, const AxisArgs& a0, int* err, 
   if (grid <= 0) return cudaSuccess;
   CUtensorMap m;
   memcpy(&m, map128, sizeof(m));
-  tpass_tma_kernel<PL, TX><<<(unsigned)grid, PL::T * TX, smem, s>>>(m, a, err);
+  tpass_tma_kernel<PL, TX><<<(unsigned)grid, PL::T * TX, smem, s>>>(m, a, err, wait_ns);
   return cudaPeekAtLastError();
 }
 
-cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err, cudaStream_t s) {
+cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err,
+                               unsigned long long wait_ns, cudaStream_t s) {
   if (tx == 8) {
     switch (nt) {
-      case 256: return launch_tma<TauPlan<256>, 8>(map128, a, err, s);
-      case 512: return launch_tma<TauPlan<512>, 8>(map128, a, err, s);
+      case 256: return launch_tma<TauPlan<256>, 8>(map128, a, err, wait_ns, s);
+      case 512: return launch_tma<TauPlan<512>, 8>(map128, a, err, wait_ns, s);
       default: return cudaErrorNotSupported;
     }
   }
   switch (nt) {
-    case 256: return launch_tma<TauPlan<256>, 16>(map128, a, err, s);
-    case 512: return launch_tma<TauPlan<512>, 16>(map128, a, err, s);
+    case 256: return launch_tma<TauPlan<256>, 16>(map128, a, err, wait_ns, s);
+    case 512: return launch_tma<TauPlan<512>, 16>(map128, a, err, wait_ns, s);
     default: return cudaErrorNotSupported;
   }
 }

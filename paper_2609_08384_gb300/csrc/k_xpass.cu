@@ -1,5 +1,6 @@
 // x-pass instantiations and dispatch.
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
 
@@ -8,13 +9,9 @@ static cudaError_t launch_x_variant(const XPassArgs& a, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(xpass_kernel<NX, F, MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(xpass_kernel<NX, F, MAP>, smem, once);
+  if (e != cudaSuccess) return e;
   const long long grid = (a.rows + ROWS - 1) / ROWS;
   if (grid <= 0) return cudaSuccess;
   xpass_kernel<NX, F, MAP><<<(unsigned)grid, THREADS, smem, s>>>(a);

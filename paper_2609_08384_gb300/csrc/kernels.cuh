@@ -534,7 +534,9 @@ int tau_col_tile_of(int n);  // columns per tile of the tau propagator kernel
 // TMA tau-pass (k_tma.cu)
 bool tma_tau_supported(int nx, int nt);
 cudaError_t make_tau_tensor_map(void* map128, const float2* data, int nx, int ny, int nt, int nf, int tx);
-cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err, cudaStream_t s);
+// wait_ns bounds each wait for a tile's copy; on expiry *err is set
+cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err,
+                               unsigned long long wait_ns, cudaStream_t s);
 
 // per-pass twiddle table of the default plan of length n (host-built, FP64
 // split into hi + lo floats), and its size in float4 entries

@@ -19,6 +19,7 @@
 // k_xadj.cu (map-free) and k_xadj_map.cu.
 #pragma once
 
+#include "launch_cfg.h"
 #include "vjp.cuh"
 
 namespace brahms {
@@ -193,13 +194,9 @@ cudaError_t launch_adjoint(const XAdjArgs& a, long long* ncta, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e =
-        cudaFuncSetAttribute(xpass_adj_kernel<NX, F, MAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(xpass_adj_kernel<NX, F, MAP>, smem, once);
+  if (e != cudaSuccess) return e;
   const long long grid = (a.rows + ROWS - 1) / ROWS;
   *ncta = grid;
   if (grid <= 0) return cudaSuccess;

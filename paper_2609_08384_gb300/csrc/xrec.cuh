@@ -4,6 +4,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "launch_cfg.h"
 
 namespace brahms {
 
@@ -12,13 +13,9 @@ cudaError_t launch_record(const XPassArgs& a, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(xpass_kernel<NX, F, MAP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(xpass_kernel<NX, F, MAP, true>, smem, once);
+  if (e != cudaSuccess) return e;
   const long long grid = (a.rows + ROWS - 1) / ROWS;
   if (grid <= 0) return cudaSuccess;
   xpass_kernel<NX, F, MAP, true><<<(unsigned)grid, THREADS, smem, s>>>(a);

@@ -54,7 +54,7 @@ def test_status_strings_without_gpu(lib):
 CTX_CALLS = ["brahms_set_fields", "brahms_set_dk_profile", "brahms_propagate", "brahms_get_fields", "brahms_energy",
              "brahms_sync", "brahms_transform", "brahms_set_dk_map", "brahms_diagnostics", "brahms_heat_accumulate",
              "brahms_heat_set", "brahms_thermal_map", "brahms_get_z", "brahms_timing", "brahms_set_option",
-             "brahms_adjoint_forward", "brahms_adjoint_backward"]
+             "brahms_adjoint_forward", "brahms_adjoint_backward", "brahms_shg_efficiency_weights"]
 
 
 def test_null_context_is_an_argument_error_without_gpu(lib):
@@ -75,3 +75,25 @@ def test_null_context_is_an_argument_error_without_gpu(lib):
     fn = lib.brahms_launch_count
     fn.restype, fn.argtypes = ctypes.c_longlong, [ctypes.c_void_p]
     assert fn(None) == 0
+
+
+def test_allocation_failure_hook_without_gpu(lib):
+    """brahms_fail_next_allocations: the next allocations report E_OOM before
+    the CUDA allocator is called (so this runs without a GPU), each failure is
+    consumed once, and a negative count is an argument error."""
+    import paper_2609_08384_gb300 as br
+    for name in ("brahms_fail_next_allocations", "brahms_pending_allocation_failures", "brahms_batch_create",
+                 "brahms_batch_set_timeout"):
+        restype, argtypes = br.SIGNATURES[name]
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = restype, argtypes
+    assert lib.brahms_fail_next_allocations(-1) == 1
+    assert lib.brahms_fail_next_allocations(2) == 0
+    assert lib.brahms_pending_allocation_failures() == 2
+    out = ctypes.c_void_p()
+    assert lib.brahms_batch_create(ctypes.byref(out), None) == 4  # its pinned status word
+    assert not out.value
+    assert lib.brahms_pending_allocation_failures() == 1
+    assert lib.brahms_fail_next_allocations(0) == 0
+    assert lib.brahms_pending_allocation_failures() == 0
+    assert lib.brahms_batch_set_timeout(None, 1.0) == 1

@@ -108,9 +108,12 @@ def test_adjoint_gradient_full_size_directional_derivative():
     F = wl.focused_pulse(p.grid, f[1], a0, 50 * wl.UM, 200 * wl.FS, p.length).astype(np.complex64)
     ins = [np.zeros_like(F), F]
     phi, dk = p.spectral_phase, p.dk_profile
-    w = br.shg_efficiency_weights(f, F.astype(np.complex128))
     s = br.Solver(p.grid, f, p.d_eff, 0.0)
     dev = [torch.from_numpy(a).cuda() for a in ins]
+    w = s.shg_efficiency_weights(dev)
+    # the library's weights are those of the definition eta = E_SH(L)/E_F(0)
+    w_def = f[0].n / (f[1].n * float(np.sum(np.abs(F.astype(np.complex128)) ** 2)))
+    assert abs(w[0] / w_def - 1) < 1e-12 and w[1] == 0.0
     J = s.adjoint_forward(dev, dk, p.nz, p.dz, w, phi=phi)
     gphi, gdk = s.adjoint_backward(1.0)
     assert 0.01 < J < 1.0
@@ -136,9 +139,9 @@ def test_autograd_function():
     import paper_2609_08384_gb300 as br
     nz, dz = 20, 20 * wl.UM
     g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 70)
-    w = br.shg_efficiency_weights(f, ins[1].astype(np.complex128))
     s = br.Solver(g, f, wl.D_EFF, 0.0)
     dev = [torch.from_numpy(a).cuda() for a in ins]
+    w = s.shg_efficiency_weights(dev)
     Eta = br.shg_efficiency_function()
     tphi = torch.tensor(phi, dtype=torch.float64, requires_grad=True)
     tdk = torch.tensor(dk, dtype=torch.float64, requires_grad=True)
