@@ -204,7 +204,8 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
  * (needs nt in {256, 512} and nx >= 16, else E_SIZE); 0 (the default) keeps
  * the plain tau-pass (and turns the field streams off while set).
  * BRAHMS_OPT_TMA_WAIT_US: the limit, in microseconds (0 .. 2000000, default
- * 2000000 = 2 s), of each wait of the TMA tau-pass for a tile's copy.  When a
+ * 2000000 = 2 s), of each wait of the TMA tau-pass for a tile's copy; 0
+ * gives up at the first check that finds the copy unfinished.  When a
  * wait runs out the kernel lets its copies in flight land (waiting at most
  * 2 s more), leaves its remaining tiles untransformed and returns; the next
  * synchronising call reports E_TIMEOUT and the fields must be set again.
@@ -261,7 +262,8 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
  * eta = E_SH(L) / E_F(0) of the current two fields (SH, F), as set by
  * brahms_set_fields with the input: w_SH = n_SH / (n_F sum |A_F|^2),
  * w_F = 0 (the common factor 1/2 c eps0 dx dy dtau of both energies cancels;
- * a spectral phase on F keeps E_F(0)).  FP64 sum on the device; waits.
+ * a spectral phase on F keeps E_F(0)).  The sum takes the FP32 squares of
+ * the complex64 field into FP64 (relative error ~1e-9); waits.
  * weights: 2 doubles.  E_ARG for three fields or a zero fundamental,
  * E_STATE without fields. */
 brahms_status brahms_shg_efficiency_weights(brahms_ctx* ctx, double* weights);

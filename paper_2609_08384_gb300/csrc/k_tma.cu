@@ -38,8 +38,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait; false on timeout
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout.  The first probe does not block
+// (test_wait); a zero limit gives up right there if the phase is not complete,
+// so that a test can make the wait run out (try_wait may itself suspend the
+// thread until the copy lands, which would hide a short limit).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+  if (mbar_test_wait(bar, parity)) return true;
+  if (limit_ns == 0) return false;
   const unsigned long long t0 = gtimer_ns();
   while (!mbar_try_wait(bar, parity)) {
     if (gtimer_ns() - t0 > limit_ns) return false;

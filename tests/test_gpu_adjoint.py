@@ -112,8 +112,9 @@ def test_adjoint_gradient_full_size_directional_derivative():
     dev = [torch.from_numpy(a).cuda() for a in ins]
     w = s.shg_efficiency_weights(dev)
     # the library's weights are those of the definition eta = E_SH(L)/E_F(0)
+    # (its sum takes FP32 squares of the complex64 field into FP64: ~1e-9)
     w_def = f[0].n / (f[1].n * float(np.sum(np.abs(F.astype(np.complex128)) ** 2)))
-    assert abs(w[0] / w_def - 1) < 1e-12 and w[1] == 0.0
+    assert abs(w[0] / w_def - 1) < 1e-7 and w[1] == 0.0
     J = s.adjoint_forward(dev, dk, p.nz, p.dz, w, phi=phi)
     gphi, gdk = s.adjoint_backward(1.0)
     assert 0.01 < J < 1.0
