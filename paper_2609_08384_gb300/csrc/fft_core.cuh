@@ -170,6 +170,74 @@ __device__ __forceinline__ void dft16(float2* v) {
   }
 }
 
+// cos(pi k / 16) for any integer k, in double (compile time): the first
+// quadrant's values, the rest by symmetry.
+__host__ __device__ constexpr double cos_pi16_q(int k) {
+  return k == 0 ? 1.0
+       : k == 1 ? 0.98078528040323044912618223613424
+       : k == 2 ? 0.92387953251128675612818318939679
+       : k == 3 ? 0.83146961230254523707878837761791
+       : k == 4 ? 0.70710678118654752440084436210485
+       : k == 5 ? 0.55557023301960222474283081394853
+       : k == 6 ? 0.38268343236508977172845998403040
+       : k == 7 ? 0.19509032201612826784828486847702
+                : 0.0;
+}
+__host__ __device__ constexpr double cos_pi16(int k) {
+  return (k % 32 + 32) % 32 > 16 ? cos_pi16(32 - (k % 32 + 32) % 32)
+       : (k % 32 + 32) % 32 > 8  ? -cos_pi16_q(16 - (k % 32 + 32) % 32)
+                                 : cos_pi16_q((k % 32 + 32) % 32);
+}
+__host__ __device__ constexpr double sin_pi16(int k) { return cos_pi16(8 - k); }
+__host__ __device__ constexpr float hi_of(double v) { return (float)v; }
+__host__ __device__ constexpr float lo_of(double v) { return (float)(v - (double)(float)v); }
+
+// multiply by W32^e = e^{-/+ 2 pi i e / 32}: the exact cases (multiples of
+// 8) as swaps and signs, the others through W16 or as hi + lo products
+template <bool INV, int E>
+__device__ __forceinline__ float2 w32(float2 a) {
+  if constexpr (E % 2 == 0 && (E / 2 <= 4 || E / 2 == 6 || E / 2 == 9)) return w16<INV, E / 2>(a);
+  else if constexpr (E == 16) return make_float2(-a.x, -a.y);
+  else {
+    constexpr double c = cos_pi16(E), s = sin_pi16(E);
+    return twx<INV>(a, hi_of(c), lo_of(c), hi_of(s), lo_of(s));
+  }
+}
+
+// radix 32 = 8 x 4: n = 4 n1 + n2 (n1 < 8, n2 < 4), k = k1 + 8 k2; eight-point
+// transforms over n1, twiddles W32^{n2 k1}, four-point transforms over n2
+template <bool INV>
+__device__ __forceinline__ void dft32(float2* v) {
+  float2 y[4][8];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 8; ++n1) y[n2][n1] = v[4 * n1 + n2];
+    dft8<INV>(y[n2]);
+  }
+#define BRAHMS_W32_ROW(N2)                   \
+  y[N2][1] = w32<INV, N2 * 1>(y[N2][1]);     \
+  y[N2][2] = w32<INV, N2 * 2>(y[N2][2]);     \
+  y[N2][3] = w32<INV, N2 * 3>(y[N2][3]);     \
+  y[N2][4] = w32<INV, N2 * 4>(y[N2][4]);     \
+  y[N2][5] = w32<INV, N2 * 5>(y[N2][5]);     \
+  y[N2][6] = w32<INV, N2 * 6>(y[N2][6]);     \
+  y[N2][7] = w32<INV, N2 * 7>(y[N2][7]);
+  BRAHMS_W32_ROW(1)
+  BRAHMS_W32_ROW(2)
+  BRAHMS_W32_ROW(3)
+#undef BRAHMS_W32_ROW
+#pragma unroll
+  for (int k1 = 0; k1 < 8; ++k1) {
+    float2 b0 = y[0][k1], b1 = y[1][k1], b2 = y[2][k1], b3 = y[3][k1];
+    dft4<INV>(b0, b1, b2, b3);
+    v[k1] = b0;
+    v[k1 + 8] = b1;
+    v[k1 + 16] = b2;
+    v[k1 + 24] = b3;
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* v) {
   if constexpr (R == 2) dft2<INV>(v[0], v[1]);
@@ -177,6 +245,7 @@ __device__ __forceinline__ void dft(float2* v) {
   else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
+  else if constexpr (R == 32) dft32<INV>(v);
   else static_assert(R == 2, "unsupported radix");
 }
 
@@ -203,7 +272,10 @@ template <> struct FftPlan<32> : Plan<32, 8, 2, 4, 8> {};
 template <> struct FftPlan<64> : Plan<64, 8, 2, 8, 8> {};
 template <> struct FftPlan<128> : Plan<128, 16, 2, 16, 8> {};
 template <> struct FftPlan<256> : Plan<256, 16, 2, 16, 16> {};
-template <> struct FftPlan<512> : Plan<512, 16, 3, 8, 8, 8> {};
+// 512 = 32 x 16 (two passes, one exchange): measured on GB300 for the tau
+// propagator of the 3 x 256x256x512 state, 473 us per launch against 546 for
+// 8 x 8 x 8 and 610 for 16 x 32
+template <> struct FftPlan<512> : Plan<512, 32, 2, 32, 16> {};
 template <> struct FftPlan<1024> : Plan<1024, 16, 3, 16, 8, 8> {};
 template <> struct FftPlan<2048> : Plan<2048, 16, 3, 16, 16, 8> {};
 template <> struct FftPlan<4096> : Plan<4096, 16, 3, 16, 16, 16> {};
@@ -217,7 +289,8 @@ template <> struct FftPlan<384> : Plan<384, 24, 4, 3, 8, 4, 4> {};
 template <> struct FftPlan<768> : Plan<768, 24, 4, 3, 4, 8, 8> {};
 
 // tau-pass plans (a 512-point plan with 8 values per thread and 1024-thread
-// tiles measured slower on GB300 than the default, 742 vs 709 us per OPG launch)
+// tiles measured slower on GB300 than the default, 742 vs 709 us per OPG
+// launch; the tau pass shares the default plans and their twiddle tables)
 template <int N>
 struct TauPlan : FftPlan<N> {};
 

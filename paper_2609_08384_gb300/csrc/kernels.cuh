@@ -376,7 +376,8 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_min_blocks<NX, F>()
   float2* rowbuf = coef + 6 * F;
   if constexpr (!MAP) nl_coefficients<F>(p, coef);
   __syncthreads();
-  xpass_tile<NX, F, THREADS, MAP, REC>(p, blockIdx.x, coef, rowbuf);
+  // rows from the last tau-plane down (see the note on pass order above)
+  xpass_tile<NX, F, THREADS, MAP, REC>(p, (long long)gridDim.x - 1 - blockIdx.x, coef, rowbuf);
 }
 
 // w (1 + d) for a propagator factor in delta form: the small product w d is
@@ -390,6 +391,13 @@ __device__ __forceinline__ float2 mul_one_plus(float2 w, float2 d) { return cadd
 // ------------------------------------------------- strided-axis passes
 // AXIS 1: pencils along y (stride nx), tiles over (f, tau, x-tile).
 // AXIS 2: pencils along tau (stride nx ny), tiles over (f, y, x-tile).
+// Order across passes: the x-pass walks its rows from the last tau-plane
+// down and the y-passes from the first up, so the x-pass starts on planes the
+// y-inverse wrote last and the y-forward on planes the x-pass wrote last,
+// still in L2 (read there, and overwritten there before they are written
+// back).  Measured on the 3 x 256x256x512 state: 1603 -> 1592 ms per
+// 1000-step call; a tau-major y order (every field of a plane together)
+// made the y-passes 20 us slower and the step 1622 ms.
 template <int N, int AXIS, int TX>
 struct AxisTile {
   float2* base;  // element (x, pencil index 0)
