@@ -258,6 +258,7 @@ def batched_form(dev, reps=2, small=False):
     b.tune(16)
     t_tune = time.perf_counter() - t_tune
     sched = {s: b.schedule(s) for s in range(4)}
+    mode = {1: "grouped", 2: "persistent"}.get(b.mode(), "?")
 
     def one():
         for i, x in enumerate(ins):
@@ -290,6 +291,7 @@ def batched_form(dev, reps=2, small=False):
     for s_ in solvers:
         s_.close()
     return {"value": units / (ms_batch / 1e3), "unit": UNIT, "ms": ms_batch, "instances": len(probs),
+            "form": mode, "kernel_launches_per_run": info["launches"] / (reps + 1),
             "persistent_grid": info["grid"], "schedule_by_shape": sched, "tune_s": t_tune,
             "sequential_single_instance": {"value": units / (ms_seq / 1e3), "ms": ms_seq},
             "speedup_vs_sequential": ms_seq / ms_batch,

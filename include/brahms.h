@@ -270,13 +270,24 @@ brahms_status brahms_shg_efficiency_weights(brahms_ctx* ctx, double* weights);
 
 /* ------------------------------------------------------------------------
  * Batched form (two-field SHG sweeps): many independent simulations of
- * uneven grids, mismatch and crystal length advanced by one persistent
- * cooperative kernel whose launch is captured in a CUDA graph.  Each instance
- * follows the same split step as brahms_propagate (constant dk per instance,
- * starting at z = 0 with Phi = 0).  Shapes (nx = ny, nt) must be one of
- * (32,64), (64,128), (96,192), (128,256) (else E_SIZE).  The batch allocates
- * its own device memory (state and tables per instance).  Work is enqueued on
- * cuda_stream (NULL = legacy default stream).
+ * uneven grids, mismatch and crystal length, run by one CUDA graph launch.
+ * Each instance follows the same split step as brahms_propagate (constant dk
+ * per instance, starting at z = 0 with Phi = 0) and gives its numbers bit for
+ * bit.  Two forms (brahms_batch_set_mode):
+ *   grouped (1): the instances of one grid shape are stored one after
+ *     another and every pass of all of them is one launch of the
+ *     single-instance kernels; each shape's launches run on a stream of
+ *     their own, so passes of different shapes overlap.  Any grid the
+ *     single-instance path supports with ny, nt >= 2 can join.
+ *   persistent (2): one persistent cooperative kernel with a work queue of
+ *     (instance, pass, tile range) items and per-instance bounded pass
+ *     barriers; shapes (nx = ny, nt) in (32,64), (64,128), (96,192),
+ *     (128,256) only.
+ *   automatic (0, the default): the grouped form until brahms_batch_tune
+ *     has timed both and kept the faster.
+ * The batch allocates its own device memory (state and tables per instance,
+ * regrouped by shape at the first run after instances were added).  Work is
+ * enqueued on cuda_stream (NULL = legacy default stream).
  * ---------------------------------------------------------------------- */
 typedef struct brahms_batch brahms_batch;
 
@@ -284,7 +295,10 @@ typedef struct brahms_batch brahms_batch;
 brahms_status brahms_batch_create(brahms_batch** out, void* cuda_stream);
 
 /* Add one SHG instance (fields SH, F; fp holds 2 records) that will run nz
- * steps of dz [m]; *index receives its position.  Tables are built here. */
+ * steps of dz [m]; *index receives its position.  Tables are built here.
+ * E_SIZE for grid lengths the single-instance path does not support, for
+ * ny or nt = 1, and, once the persistent form is set, for a shape outside
+ * its four. */
 brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double dx, double dy, double dt,
                                const brahms_field_params* fp, double d_eff, double dk, int nz, double dz,
                                int* index);
@@ -295,24 +309,33 @@ brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double d
 brahms_status brahms_batch_set_fields(brahms_batch* b, int index, const void* const* fields, int dtype,
                                       int on_device);
 
-/* Tile schedule of one shape (0..3 in the order above): CTA tiles per work
- * item for the x-, y- and tau-passes (1..64). */
+/* Tile schedule of the persistent form for one of its shapes (0..3 in the
+ * order above): CTA tiles per work item for the x-, y- and tau-passes
+ * (1..64). */
 brahms_status brahms_batch_set_granularity(brahms_batch* b, int shape, int gx, int gy, int gt);
 
-/* Autotune the schedule: per shape the tiles per item (one of 1, 2, 4, 8, 16
- * for all three passes, then each pass's doubled or halved while that helps,
- * within 1..64), then CTAs per SM (1, 2), each timed on the whole batch with
- * every instance capped at
- * tune_steps steps; instance fields are restored afterwards.  Waits for the
- * stream.  *best_ms (nullable) receives the best capped run time. */
+/* Autotune: each trial times the whole batch with every instance capped at
+ * tune_steps steps (fields restored afterwards).  The grouped form is timed
+ * once; the persistent form, where its shapes allow it, is searched: per
+ * shape the tiles per item (one of 1, 2, 4, 8, 16 for all three passes,
+ * then each pass's doubled or halved while that helps, within 1..64), then
+ * CTAs per SM (1, 2).  In the automatic mode the faster form is kept.
+ * Waits for the stream.  *best_ms (nullable) receives the best capped run
+ * time. */
 brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms);
 
 /* The current schedule of one shape. */
 brahms_status brahms_batch_get_schedule(const brahms_batch* b, int shape, int* gx, int* gy, int* gt,
                                         int* ctas_per_sm);
 
+/* Form of the batch: 0 automatic, 1 grouped, 2 persistent (E_SIZE if an
+ * instance's shape is not one of the persistent form's); E_ARG otherwise.
+ * brahms_batch_get_mode returns the form the next run uses (1 or 2). */
+brahms_status brahms_batch_set_mode(brahms_batch* b, int mode);
+int brahms_batch_get_mode(const brahms_batch* b);
+
 /* Advance every instance through all of its nz steps (z = 0 to nz dz) in one
- * graph launch: counter reset + the persistent kernel.  Asynchronous. */
+ * graph launch.  Asynchronous. */
 brahms_status brahms_batch_run(brahms_batch* b);
 
 /* Wait for the stream; E_TIMEOUT if the persistent kernel gave up waiting
@@ -331,7 +354,8 @@ brahms_status brahms_batch_set_timeout(brahms_batch* b, double seconds);
 /* Copy instance `index`'s envelopes out (2 pointers, complex64); waits. */
 brahms_status brahms_batch_get_fields(brahms_batch* b, int index, void* const* out, int dtype, int on_device);
 
-/* Instances, persistent grid size, threads per CTA, graph launches so far. */
+/* Instances, persistent grid size (0 in the grouped form), threads per CTA
+ * of the persistent kernel, kernel launches made by the runs so far. */
 brahms_status brahms_batch_info(const brahms_batch* b, int* ninstances, int* grid, int* threads,
                                 long long* launches);
 

@@ -86,6 +86,8 @@ SIGNATURES = {
     "brahms_batch_run": (_c.c_int, [_vp]),
     "brahms_batch_sync": (_c.c_int, [_vp]),
     "brahms_batch_set_timeout": (_c.c_int, [_vp, _c.c_double]),
+    "brahms_batch_set_mode": (_c.c_int, [_vp, _c.c_int]),
+    "brahms_batch_get_mode": (_c.c_int, [_vp]),
     "brahms_batch_get_fields": (_c.c_int, [_vp, _c.c_int, _c.POINTER(_vp), _c.c_int, _c.c_int]),
     "brahms_batch_info": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int),
                                      _llp]),
@@ -433,6 +435,13 @@ class Batch:
 
     def sync(self):
         self._chk(load().brahms_batch_sync(self.h))
+
+    def set_mode(self, mode: int):
+        """0 automatic (the tuner picks), 1 grouped, 2 persistent."""
+        self._chk(load().brahms_batch_set_mode(self.h, int(mode)))
+
+    def mode(self) -> int:
+        return int(load().brahms_batch_get_mode(self.h))
 
     def set_timeout(self, seconds: float):
         """Limit of each bounded wait of the persistent kernel (default 5 s)."""

@@ -1,6 +1,20 @@
 // Batched form: many independent two-field (SH, F) split-step simulations of
-// uneven grids, mismatch and crystal length, advanced by ONE persistent
-// cooperative kernel, the launch captured in a CUDA graph.
+// uneven grids, mismatch and crystal length, run from one CUDA graph launch
+// in one of two forms, which the autotuner chooses between by timing both:
+//
+// Grouped.  The instances of one grid shape are stored one after another, so
+// that a pass of all of them is one launch of the single-instance kernels
+// (the y- and tau-passes see the instances' fields as more fields; the x-pass
+// takes each instance's step, coupling and mismatch from a table).  Per shape
+// the instances are ordered by step count, longest first, so the ones still
+// running at step j are a prefix: step j is four launches over that prefix.
+// Each shape's launch sequence runs on a stream of its own inside the graph,
+// so the passes of different shapes overlap (a DRAM-bound pass of one beside
+// an issue-bound pass of another).  Any shape the single-instance path
+// supports (ny, nt >= 2) can join.
+//
+// Persistent (the four compiled shapes below only): ONE persistent
+// cooperative kernel advances every instance.
 //
 // Work queue.  Each instance's propagation is a fixed sequence of passes:
 //   x(first half step of step 0), then per step j: y-forward, tau-propagator,
@@ -370,10 +384,10 @@ constexpr double kTwoPi = 6.283185307179586476925286766559;
 using namespace brahms;
 
 struct BatchInstHost {
-  int nx, ny, nt, shape, nz;
+  int nx, ny, nt, shape, nz;  // shape: index into the persistent kernel's shapes, -1 if not one of them
   double dx, dy, dt, dz, dk, d_eff;
   brahms_field_params fp[2];
-  char* mem = nullptr;  // state + tables
+  char* mem = nullptr;  // state + tables until the instance joins a group (then NULL)
   float2* state = nullptr;
   float4 *twx = nullptr, *twt = nullptr;
   float2 *px = nullptr, *py = nullptr, *pt = nullptr;
@@ -381,9 +395,33 @@ struct BatchInstHost {
   long long npoints() const { return (long long)nx * ny * nt; }
 };
 
+// The instances of one grid shape, stored one after another in sorted order
+// (step count, longest first): state [slot][2][nt][ny][nx], propagator
+// tables [2 slot + f][n] per axis, the shape's twiddles, the per-instance
+// table of the grouped x-pass.
+struct BatchGroup {
+  int nx, ny, nt;
+  std::vector<int> members;  // instance indices in slot order
+  char* mem = nullptr;
+  float2* state = nullptr;
+  float2 *px = nullptr, *py = nullptr, *pt = nullptr;
+  float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
+  GroupInst* params = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  long long npoints() const { return (long long)nx * ny * nt; }
+};
+
+enum { kModeAuto = 0, kModeGrouped = 1, kModePersistent = 2 };
+
 struct brahms_batch {
   cudaStream_t stream = nullptr;
   std::vector<BatchInstHost> inst;
+  std::vector<BatchGroup> groups;
+  bool layout_dirty = true;
+  int mode = kModeAuto;   // asked for (brahms_batch_set_mode)
+  int chosen = kModeGrouped;  // what an automatic mode runs (set by the tuner)
+  cudaEvent_t ev_fork = nullptr;
   std::string err;
   int gran[kNumShapes][3];  // tiles per item (x, y, t) per shape
   int ctas_per_sm = 1;
@@ -402,7 +440,8 @@ struct brahms_batch {
   int grid = 0;
   size_t smem = 0;
   double timeout_s = 5.0;
-  long long launches = 0;
+  long long launches = 0;        // kernel launches made by graph launches so far
+  long long graph_launches = 0;  // kernel launches in one graph launch
 };
 
 namespace {
@@ -437,11 +476,290 @@ void free_device(brahms_batch* b) {
   b->d_inst = nullptr;
   b->d_next = nullptr;
   b->d_done = nullptr;
+  b->d_status = nullptr;  // lives in d_done's allocation
 }
+
+void free_groups(brahms_batch* b) {
+  for (auto& g : b->groups) {
+    cudaFree(g.mem);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
+  }
+  b->groups.clear();
+}
+
+brahms_status build_tables_for(brahms_batch* b, BatchInstHost& I);
+
+bool persistent_possible(const brahms_batch* b) {
+  for (auto& I : b->inst)
+    if (I.shape < 0) return false;
+  return true;
+}
+
+int effective_nz(const brahms_batch* b, const BatchInstHost& I) {
+  return b->nz_cap > 0 ? std::min(I.nz, b->nz_cap) : I.nz;
+}
+
+// Group the instances by shape into arrays of their own (see BatchGroup):
+// the fields move there, the tables are rebuilt there, and every instance's
+// pointers (used by both forms) point into its group.
+brahms_status layout(brahms_batch* b) {
+  std::vector<BatchGroup> gs;
+  for (int i = 0; i < (int)b->inst.size(); ++i) {
+    const BatchInstHost& I = b->inst[i];
+    int g = -1;
+    for (int k = 0; k < (int)gs.size(); ++k)
+      if (gs[k].nx == I.nx && gs[k].ny == I.ny && gs[k].nt == I.nt) g = k;
+    if (g < 0) {
+      gs.push_back(BatchGroup{});
+      g = (int)gs.size() - 1;
+      gs[g].nx = I.nx;
+      gs[g].ny = I.ny;
+      gs[g].nt = I.nt;
+    }
+    gs[g].members.push_back(i);
+  }
+  auto release = [&](brahms_status s) {
+    for (auto& g : gs) {
+      cudaFree(g.mem);
+      if (g.stream) cudaStreamDestroy(g.stream);
+      if (g.done) cudaEventDestroy(g.done);
+    }
+    return s;
+  };
+  for (auto& g : gs) {
+    std::stable_sort(g.members.begin(), g.members.end(),
+                     [&](int a, int c) { return b->inst[a].nz > b->inst[c].nz; });
+    const size_t m = g.members.size(), n = (size_t)g.npoints();
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+      size_t o = off;
+      off += al256(bytes);
+      return o;
+    };
+    const size_t o_state = take(sizeof(float2) * 2 * n * m), o_px = take(sizeof(float2) * 2 * m * g.nx),
+                 o_py = take(sizeof(float2) * 2 * m * g.ny), o_pt = take(sizeof(float2) * 2 * m * g.nt),
+                 o_twx = take(sizeof(float4) * tw_table_size_of(g.nx)),
+                 o_twy = take(sizeof(float4) * tw_table_size_of(g.ny)),
+                 o_twt = take(sizeof(float4) * tw_table_size_of(g.nt)), o_par = take(sizeof(GroupInst) * m);
+    if (dev_alloc((void**)&g.mem, off) != cudaSuccess) {
+      cudaGetLastError();
+      return release(bfail(b, BRAHMS_E_OOM, "batch group memory"));
+    }
+    g.state = (float2*)(g.mem + o_state);
+    g.px = (float2*)(g.mem + o_px);
+    g.py = (float2*)(g.mem + o_py);
+    g.pt = (float2*)(g.mem + o_pt);
+    g.twx = (float4*)(g.mem + o_twx);
+    g.twy = (float4*)(g.mem + o_twy);
+    g.twt = (float4*)(g.mem + o_twt);
+    g.params = (GroupInst*)(g.mem + o_par);
+    if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
+      return release(bfail(b, BRAHMS_E_CUDA, "group stream"));
+    cudaError_t e = upload_twiddles(g.twx, g.nx, b->stream);
+    if (e == cudaSuccess) e = upload_twiddles(g.twy, g.ny, b->stream);
+    if (e == cudaSuccess) e = upload_twiddles(g.twt, g.nt, b->stream);
+    if (e != cudaSuccess) return release(bfail(b, BRAHMS_E_CUDA, std::string("twiddles: ") + cudaGetErrorString(e)));
+    for (size_t slot = 0; slot < m; ++slot) {
+      BatchInstHost& I = b->inst[g.members[slot]];
+      float2* dst = g.state + slot * 2 * n;
+      if (I.have_fields && I.state) {
+        e = cudaMemcpyAsync(dst, I.state, sizeof(float2) * 2 * n, cudaMemcpyDeviceToDevice, b->stream);
+        if (e != cudaSuccess) return release(bfail(b, BRAHMS_E_CUDA, cudaGetErrorString(e)));
+      }
+    }
+  }
+  // the copies out of the old locations are done before those are released
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return release(bfail(b, BRAHMS_E_CUDA, "layout copy"));
+  free_groups(b);
+  for (auto& g : gs) {
+    const size_t n = (size_t)g.npoints();
+    for (size_t slot = 0; slot < g.members.size(); ++slot) {
+      BatchInstHost& I = b->inst[g.members[slot]];
+      if (I.mem) cudaFree(I.mem);
+      I.mem = nullptr;
+      I.state = g.state + slot * 2 * n;
+      I.px = g.px + slot * 2 * g.nx;
+      I.py = g.py + slot * 2 * g.ny;
+      I.pt = g.pt + slot * 2 * g.nt;
+      I.twx = g.twx;
+      I.twt = g.twt;
+      brahms_status st = build_tables_for(b, I);
+      if (st != BRAHMS_OK) {
+        b->groups = gs;
+        return st;
+      }
+    }
+  }
+  b->groups = gs;
+  b->layout_dirty = false;
+  return BRAHMS_OK;
+}
+
+// one graph launch: per group, on the group's stream, the first x-pass of
+// every instance, then per step j the y-forward, tau-propagator, y-inverse
+// and x-pass of the instances still running at step j
+brahms_status prepare_grouped(brahms_batch* b) {
+  BB_CK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming)) ;
+  for (auto& g : b->groups) {
+    std::vector<GroupInst> h(g.members.size());
+    for (size_t slot = 0; slot < g.members.size(); ++slot) {
+      const BatchInstHost& I = b->inst[g.members[slot]];
+      GroupInst& p = h[slot];
+      for (int f = 0; f < 2; ++f) {
+        double k = kTwoPi * I.d_eff / (I.fp[f].n * I.fp[f].lambda);
+        if (f == 0) k *= 0.5;  // degenerate SHG: 1/2 on the SH equation
+        p.kh[f] = (float)(k * 0.5 * I.dz);
+        p.kh2[f] = 0.5f * p.kh[f];
+      }
+      p.dk = I.dk;
+      p.dz = I.dz;
+      p.nz = effective_nz(b, I);
+    }
+    BB_CK(cudaMemcpyAsync(g.params, h.data(), sizeof(GroupInst) * h.size(), cudaMemcpyHostToDevice, b->stream));
+    BB_CK(cudaStreamSynchronize(b->stream));  // h is a local buffer
+  }
+  // configure every kernel outside the capture (no work: empty ranges)
+  for (auto& g : b->groups) {
+    AxisArgs z{};
+    z.nx = g.nx;
+    z.ny = g.ny;
+    z.nt = g.nt;
+    z.xtiles = 1;
+    BB_CK(run_axis_fft(g.ny, 1, false, z, b->stream));
+    BB_CK(run_axis_fft(g.ny, 1, true, z, b->stream));
+    BB_CK(run_tpass_prop(g.nt, z, b->stream));
+    XPassArgs x{};
+    BB_CK(run_xpass_group(g.nx, x, g.params, 0, 0, b->stream));
+    BB_CK(run_xpass(g.nx, 2, x, b->stream));
+  }
+  cudaStream_t cap = nullptr;
+  BB_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(b->ev_fork, cap);
+  long long nl = 0;
+  for (auto& g : b->groups) {
+    if (e != cudaSuccess) break;
+    cudaStream_t s = g.stream;
+    e = cudaStreamWaitEvent(s, b->ev_fork, 0);
+    const long long n = g.npoints();
+    const int m = (int)g.members.size();
+    const int rows = xpass_rows_of(g.nx);
+    const bool whole = rows > 0 && ((long long)g.ny * g.nt) % rows == 0;
+    std::vector<int> nzs(m);
+    int nz_max = 0;
+    for (int slot = 0; slot < m; ++slot) {
+      nzs[slot] = effective_nz(b, b->inst[g.members[slot]]);
+      nz_max = std::max(nz_max, nzs[slot]);
+    }
+    XPassArgs base{};
+    base.data = g.state;
+    base.fstride = n;
+    base.rows = (long long)g.ny * g.nt;
+    base.tw = g.twx;
+    base.scale = 1.f;
+    base.ny = g.ny;
+    // an x-pass over the first a slots (per instance where an instance's rows
+    // do not fill whole CTAs)
+    auto xpass = [&](int step, int a) -> cudaError_t {
+      if (whole) return run_xpass_group(g.nx, base, g.params, step, a, s);
+      for (int slot = 0; slot < a; ++slot) {
+        const BatchInstHost& I = b->inst[g.members[slot]];
+        XPassArgs p = base;
+        p.data = g.state + (long long)slot * 2 * n;
+        p.dz = I.dz;
+        for (int f = 0; f < 2; ++f) {
+          double k = kTwoPi * I.d_eff / (I.fp[f].n * I.fp[f].lambda);
+          if (f == 0) k *= 0.5;
+          p.kh[f] = (float)(k * 0.5 * I.dz);
+          p.kh2[f] = 0.5f * p.kh[f];
+        }
+        if (step < 0) {
+          p.mode = XM_NL_FIRST;
+          p.phiA = 0.0;
+          p.dkA = I.dk;
+        } else {
+          p.mode = step == nzs[slot] - 1 ? XM_NL_LAST : XM_NL_MID;
+          p.phiB = I.dk * (step * I.dz);
+          p.dkB = I.dk;
+          p.phiA = I.dk * ((step + 1) * I.dz);
+          p.dkA = I.dk;
+        }
+        cudaError_t ee = run_xpass(g.nx, 2, p, s);
+        if (ee != cudaSuccess) return ee;
+      }
+      return cudaSuccess;
+    };
+    AxisArgs ay{};
+    ay.data = g.state;
+    ay.nx = g.nx;
+    ay.ny = g.ny;
+    ay.nt = g.nt;
+    ay.fstride = n;
+    ay.xtiles = (g.nx + col_tile_of(g.ny) - 1) / col_tile_of(g.ny);
+    ay.tw = g.twy;
+    AxisArgs at = ay;
+    at.xtiles = (g.nx + tau_col_tile_of(g.nt) - 1) / tau_col_tile_of(g.nt);
+    at.tw = g.twt;
+    at.px = g.px;
+    at.py = g.py;
+    at.pt = g.pt;
+    const double inv_n = 1.0 / (double)n;
+    at.scale = (float)inv_n;
+    at.scale_lo = (float)(inv_n - (double)at.scale);
+    if (e == cudaSuccess) e = xpass(-1, m);
+    nl += whole ? 1 : m;
+    int a = m;
+    for (int j = 0; j < nz_max && e == cudaSuccess; ++j) {
+      while (a > 0 && nzs[a - 1] <= j) --a;  // slots still running at step j
+      ay.ntiles = 2LL * a * g.nt * ay.xtiles;
+      at.ntiles = 2LL * a * g.ny * at.xtiles;
+      e = run_axis_fft(g.ny, 1, false, ay, s);
+      if (e == cudaSuccess) e = run_tpass_prop(g.nt, at, s);
+      if (e == cudaSuccess) e = run_axis_fft(g.ny, 1, true, ay, s);
+      if (e == cudaSuccess) e = xpass(j, a);
+      nl += 3 + (whole ? 1 : a);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(g.done, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cap, g.done, 0);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  if (e != cudaSuccess) return bfail(b, BRAHMS_E_CUDA, std::string("grouped graph: ") + cudaGetErrorString(e));
+  b->graph_launches = nl;
+  b->grid = 0;
+  b->dirty = false;
+  return BRAHMS_OK;
+}
+
+int run_mode(const brahms_batch* b) { return b->mode == kModeAuto ? b->chosen : b->mode; }
+
+brahms_status prepare_persistent(brahms_batch* b);
 
 brahms_status prepare(brahms_batch* b) {
   if (!b->dirty) return BRAHMS_OK;
   free_device(b);
+  if (b->ev_fork) {
+    cudaEventDestroy(b->ev_fork);
+    b->ev_fork = nullptr;
+  }
+  if (b->inst.empty()) return bfail(b, BRAHMS_E_STATE, "empty batch");
+  for (auto& I : b->inst)
+    if (!I.have_fields) return bfail(b, BRAHMS_E_STATE, "an instance has no fields");
+  if (b->layout_dirty) {
+    brahms_status s = layout(b);
+    if (s != BRAHMS_OK) return s;
+  }
+  if (run_mode(b) == kModeGrouped || !persistent_possible(b)) return prepare_grouped(b);
+  return prepare_persistent(b);
+}
+
+brahms_status prepare_persistent(brahms_batch* b) {
   const int n = (int)b->inst.size();
   if (n == 0) return bfail(b, BRAHMS_E_STATE, "empty batch");
   for (auto& I : b->inst)
@@ -544,6 +862,7 @@ brahms_status prepare(brahms_batch* b) {
   if (g) cudaGraphDestroy(g);
   cudaStreamDestroy(cap);
   if (e != cudaSuccess) return bfail(b, BRAHMS_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  b->graph_launches = 1;
   b->dirty = false;
   return BRAHMS_OK;
 }
@@ -598,6 +917,8 @@ void brahms_batch_free(brahms_batch* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   free_device(b);
+  free_groups(b);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   for (auto& I : b->inst) cudaFree(I.mem);
   cudaFreeHost(b->h_status);
   delete b;
@@ -610,8 +931,11 @@ brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double d
                                int* index) {
   if (!b) return BRAHMS_E_ARG;
   if (!fp) return bfail(b, BRAHMS_E_ARG, "fp is NULL");
+  if (!size_supported(nx) || !size_supported(ny) || !size_supported(nt) || ny < 2 || nt < 2)
+    return bfail(b, BRAHMS_E_SIZE, "batched grid lengths: the FFT lengths of the single-instance path, ny, nt >= 2");
+  if (b->mode == kModePersistent && shape_of(nx, ny, nt) < 0)
+    return bfail(b, BRAHMS_E_SIZE, "the persistent form runs the shapes (nx=ny, nt) in {(32,64),(64,128),(96,192),(128,256)} only");
   const int s = shape_of(nx, ny, nt);
-  if (s < 0) return bfail(b, BRAHMS_E_SIZE, "batched shapes: (nx=ny, nt) in {(32,64),(64,128),(96,192),(128,256)}");
   if (!(dx > 0) || !(dy > 0) || !(dt > 0) || !(dz > 0) || nz < 1 || !std::isfinite(dk) || !std::isfinite(d_eff) ||
       !std::isfinite(dz))
     return bfail(b, BRAHMS_E_ARG, "bad spacing, step or mismatch");
@@ -651,6 +975,7 @@ brahms_status brahms_batch_add(brahms_batch* b, int nx, int ny, int nt, double d
   }
   b->inst.push_back(I);
   b->dirty = true;
+  b->layout_dirty = true;
   if (index) *index = (int)b->inst.size() - 1;
   return BRAHMS_OK;
 }
@@ -696,8 +1021,25 @@ brahms_status brahms_batch_run(brahms_batch* b) {
   brahms_status s = prepare(b);
   if (s != BRAHMS_OK) return s;
   BB_CK(cudaGraphLaunch(b->exec, b->stream));
-  b->launches += 1;
+  b->launches += b->graph_launches;
   return BRAHMS_OK;
+}
+
+brahms_status brahms_batch_set_mode(brahms_batch* b, int mode) {
+  if (!b) return BRAHMS_E_ARG;
+  if (mode != kModeAuto && mode != kModeGrouped && mode != kModePersistent)
+    return bfail(b, BRAHMS_E_ARG, "mode: 0 automatic, 1 grouped, 2 persistent");
+  if (mode == kModePersistent && !persistent_possible(b))
+    return bfail(b, BRAHMS_E_SIZE, "the persistent form runs the shapes (nx=ny, nt) in {(32,64),(64,128),(96,192),(128,256)} only");
+  b->mode = mode;
+  b->dirty = true;
+  return BRAHMS_OK;
+}
+
+int brahms_batch_get_mode(const brahms_batch* b) {
+  if (!b) return -1;
+  const int m = b->mode == kModeAuto ? b->chosen : b->mode;
+  return (m == kModePersistent && !persistent_possible(b)) ? kModeGrouped : m;
 }
 
 brahms_status brahms_batch_sync(brahms_batch* b) {
@@ -733,10 +1075,11 @@ brahms_status brahms_batch_info(const brahms_batch* b, int* ninstances, int* gri
   return BRAHMS_OK;
 }
 
-// Autotuner: for each shape in the batch, the tiles per item (1, 2 or 4) and
-// then the CTAs per SM (1 or 2) are chosen by timing the whole batch with
-// every instance capped at tune_steps steps.  The fields are saved before and
-// restored after every trial.  Results are kept per (shape set, SM count).
+// Autotuner: the whole batch is timed with every instance capped at
+// tune_steps steps, the fields saved before and restored after every trial.
+// The grouped form is timed once; the persistent form (when its shapes allow
+// it) is searched: for each shape the tiles per item, then the CTAs per SM.
+// With the automatic mode the faster of the two forms is kept.
 brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms) {
   if (!b) return BRAHMS_E_ARG;
   if (b->inst.empty()) return bfail(b, BRAHMS_E_STATE, "empty batch");
@@ -784,11 +1127,21 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
   cudaError_t ce = copy_all(true);
   if (ce != cudaSuccess) st = bfail(b, BRAHMS_E_CUDA, cudaGetErrorString(ce));
   b->nz_cap = tune_steps;
+  const bool try_grouped = b->mode != kModePersistent;
+  const bool try_persistent = b->mode != kModeGrouped && persistent_possible(b);
+  float grouped_ms = 1e30f;
+  const int chosen0 = b->chosen;
+  if (try_grouped && st == BRAHMS_OK) {
+    b->chosen = kModeGrouped;
+    st = trial(&grouped_ms);
+  }
+  if (try_persistent) b->chosen = kModePersistent;
   bool present[kNumShapes] = {};
-  for (auto& I : b->inst) present[I.shape] = true;
+  for (auto& I : b->inst)
+    if (I.shape >= 0) present[I.shape] = true;
   float cur = 0.f;
-  if (st == BRAHMS_OK) st = trial(&cur);
-  for (int sh = 0; sh < kNumShapes && st == BRAHMS_OK; ++sh) {
+  if (try_persistent && st == BRAHMS_OK) st = trial(&cur);
+  for (int sh = 0; sh < kNumShapes && st == BRAHMS_OK && try_persistent; ++sh) {
     if (!present[sh]) continue;
     int keep[3] = {b->gran[sh][0], b->gran[sh][1], b->gran[sh][2]};
     // one granularity for all three passes, then a per-pass search
@@ -823,7 +1176,7 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
     b->gran[sh][1] = keep[1];
     b->gran[sh][2] = keep[2];
   }
-  if (st == BRAHMS_OK) {
+  if (st == BRAHMS_OK && try_persistent) {
     const int keep = b->ctas_per_sm;
     for (int c : {1, 2}) {
       if (c == keep) continue;
@@ -834,6 +1187,17 @@ brahms_status brahms_batch_tune(brahms_batch* b, int tune_steps, double* best_ms
       if (ms < cur) cur = ms;
       else b->ctas_per_sm = keep;
     }
+  }
+  if (st == BRAHMS_OK) {
+    if (!try_persistent) {
+      b->chosen = kModeGrouped;
+      cur = grouped_ms;
+    } else if (try_grouped && grouped_ms <= cur) {
+      b->chosen = kModeGrouped;
+      cur = grouped_ms;
+    }
+  } else {
+    b->chosen = chosen0;
   }
   b->nz_cap = 0;
   b->dirty = true;

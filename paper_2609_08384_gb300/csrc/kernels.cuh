@@ -538,6 +538,19 @@ bool size_supported(int n);
 int col_tile_of(int n);      // columns per tile of the y/tau FFT kernels
 int tau_col_tile_of(int n);  // columns per tile of the tau propagator kernel
 
+// grouped x-pass of the batched form (k_xgroup.cu): the same x-pass for
+// ninst instances of one shape stored one after another (2 fields each,
+// base.data the first, base.fstride between fields, base.rows = ny nt rows
+// per instance, base.tw the x twiddles); the instance parameters come from
+// gi[0..ninst); step < 0 is the first half step of step 0.
+struct GroupInst {
+  float kh[2], kh2[2];  // kappa_f dz/2 (1/2 on the SH equation) and half of it
+  double dk, dz;
+  int nz;
+};
+cudaError_t run_xpass_group(int nx, const XPassArgs& base, const GroupInst* gi, int step, int ninst, cudaStream_t s);
+int xpass_rows_of(int nx);  // rows per CTA of the x-pass of length nx
+
 // misc kernels (k_misc.cu)
 // TMA tau-pass (k_tma.cu)
 bool tma_tau_supported(int nx, int nt);

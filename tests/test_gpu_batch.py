@@ -1,5 +1,6 @@
-"""Batched persistent form (one cooperative launch, graph-captured) against
-the single-instance path and the FP64 oracle."""
+"""Batched form (one graph launch: grouped per-shape launches, or one
+persistent cooperative kernel) against the single-instance path and the FP64
+oracle."""
 import numpy as np
 import pytest
 
@@ -34,9 +35,14 @@ def _mixed_problems(seed=5, nz_range=(4, 14)):
     return probs
 
 
-def _run_batch(probs, inputs, tune=False):
+GROUPED, PERSISTENT = 1, 2
+
+
+def _run_batch(probs, inputs, tune=False, mode=None):
     import paper_2609_08384_gb300 as br
     b = br.Batch()
+    if mode is not None:
+        b.set_mode(mode)
     for p, inp in zip(probs, inputs):
         i = b.add(p.grid, p.fields, p.d_eff, p.dk, p.nz, p.dz)
         b.set_fields(i, [torch.from_numpy(a.astype(np.complex64)).cuda() for a in inp])
@@ -46,6 +52,7 @@ def _run_batch(probs, inputs, tune=False):
     b.sync()
     out = [b.get_fields(i) for i in range(len(probs))]
     info = b.info()
+    info["mode"] = b.mode()
     sched = [b.schedule(s) for s in range(4)]
     b.close()
     return out, info, sched
@@ -61,11 +68,13 @@ def _plain(p, inp):
     return out
 
 
-def test_batch_matches_single_instance_and_oracle():
+@pytest.mark.parametrize("mode", [GROUPED, PERSISTENT], ids=["grouped", "persistent"])
+def test_batch_matches_single_instance_and_oracle(mode):
     probs = _mixed_problems()
     inputs = [wl.inputs_shg(p) for p in probs]
-    out, info, _ = _run_batch(probs, inputs)
-    assert info["instances"] == len(probs) and info["grid"] >= 152
+    out, info, _ = _run_batch(probs, inputs, mode=mode)
+    assert info["instances"] == len(probs) and info["mode"] == mode
+    assert (info["grid"] >= 152) if mode == PERSISTENT else (info["launches"] > 4 * max(p.nz for p in probs))
     for p, inp, o in zip(probs, inputs, out):
         ref = _plain(p, inp)
         for f in range(2):
@@ -77,6 +86,56 @@ def test_batch_matches_single_instance_and_oracle():
         ref, _ = oracle.propagate(prob, [a.astype(np.complex64).astype(np.complex128) for a in inp], p.nz, p.dz, p.dk)
         for f in range(2):
             assert rel_l2(o[f], ref[f]) < 1e-4, (p.name, f)
+
+
+def test_grouped_and_persistent_forms_agree():
+    """The two forms run the same kernel code on the same tables: the results
+    agree bit for bit (up to the FP64 phase bookkeeping, which both share)."""
+    probs = _mixed_problems(seed=8)
+    inputs = [wl.inputs_shg(p) for p in probs]
+    g, _, _ = _run_batch(probs, inputs, mode=GROUPED)
+    q, _, _ = _run_batch(probs, inputs, mode=PERSISTENT)
+    for x, y in zip(g, q):
+        for f in range(2):
+            assert rel_l2(x[f], y[f]) < 1e-6
+
+
+def test_grouped_batch_takes_shapes_outside_the_persistent_four():
+    """Non-square grids and 3 * 2^k lengths outside the persistent kernel's
+    shapes: the grouped form runs them, each instance equal to the
+    single-instance path; two of them against the oracle.  Several
+    instances of one shape with different step counts exercise the shrinking
+    prefix of running instances; the persistent form refuses the set."""
+    import paper_2609_08384_gb300 as br
+    # (8, 6, 4): an instance's rows do not fill whole x-pass CTAs, so its
+    # x-passes run one instance per launch
+    shapes = [(48, 32, 96), (48, 32, 96), (96, 64, 48), (24, 48, 64), (48, 32, 96), (64, 96, 12), (8, 6, 4)]
+    rng = np.random.default_rng(11)
+    probs = []
+    for k, (nx, ny, nt) in enumerate(shapes):
+        g = wl.Grid(nx, ny, nt, 12.5 * wl.UM, 12.5 * wl.UM, 50 * wl.FS)
+        probs.append(wl.Problem(f"shg_{nx}x{ny}x{nt}_{k}", g, wl.shg_fields(), wl.D_EFF,
+                                float(rng.uniform(-200, 200)), float(rng.uniform(0.5, 2.0)) * wl.MM,
+                                int(rng.integers(5, 17))))
+    inputs = [wl.inputs_shg(p) for p in probs]
+    out, info, _ = _run_batch(probs, inputs)
+    assert info["mode"] == GROUPED
+    for p, inp, o in zip(probs, inputs, out):
+        ref = _plain(p, inp)
+        for f in range(2):
+            assert rel_l2(o[f], ref[f]) < 1e-6, (p.name, f)
+    for k in (0, 3):
+        p, inp, o = probs[k], inputs[k], out[k]
+        prob = oracle.problem_from(p)
+        ref, _ = oracle.propagate(prob, [a.astype(np.complex64).astype(np.complex128) for a in inp], p.nz, p.dz, p.dk)
+        for f in range(2):
+            assert rel_l2(o[f], ref[f]) < 1e-4, (p.name, f)
+    b = br.Batch()
+    b.add(probs[0].grid, probs[0].fields, probs[0].d_eff, probs[0].dk, probs[0].nz, probs[0].dz)
+    with pytest.raises(br.BrahmsError) as ei:
+        b.set_mode(PERSISTENT)
+    assert ei.value.status == br.BRAHMS_E_SIZE
+    b.close()
 
 
 def test_batch_repeat_is_deterministic_and_tuner_keeps_results():

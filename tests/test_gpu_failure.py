@@ -75,8 +75,9 @@ def test_tma_tau_wait_limit_runs_out_and_the_context_recovers():
     s.close()
 
 
-def _batch(br, problems):
+def _batch(br, problems, mode=0):
     b = br.Batch()
+    b.set_mode(mode)
     for p in problems:
         i = b.add(p.grid, p.fields, p.d_eff, p.dk, p.nz, p.dz)
         b.set_fields(i, [torch.from_numpy(a.astype(np.complex64)).cuda() for a in wl.inputs_shg(p)])
@@ -84,20 +85,20 @@ def _batch(br, problems):
 
 
 def test_batch_wait_limit_runs_out_and_the_batch_recovers():
-    """Persistent batched kernel with a zero wait limit: some CTA finds the
-    previous pass of an instance unfinished, its wait runs out, every CTA
-    returns and brahms_batch_sync reports E_TIMEOUT.  With the default limit
-    and the fields set again the same batch runs clean and matches a fresh
-    batch bit for bit."""
+    """Persistent batched kernel (the form with device-side waits) with a zero
+    wait limit: some CTA finds the previous pass of an instance unfinished,
+    its wait runs out, every CTA returns and brahms_batch_sync reports
+    E_TIMEOUT.  With the default limit and the fields set again the same
+    batch runs clean and matches a fresh batch bit for bit."""
     br = _br()
     probs = [wl.problem_batch_member(64, 128, 50.0, 1.0 * wl.MM, 40),
              wl.problem_batch_member(32, 64, -30.0, 0.5 * wl.MM, 25)]
-    fresh = _batch(br, probs)
+    fresh = _batch(br, probs, mode=2)
     fresh.run()
     fresh.sync()
     want = [fresh.get_fields(i) for i in range(2)]
     fresh.close()
-    b = _batch(br, probs)
+    b = _batch(br, probs, mode=2)
     b.set_timeout(0.0)
     b.run()
     with pytest.raises(br.BrahmsError) as ei:
