@@ -12,7 +12,7 @@ static cudaError_t launch_axis(const AxisArgs& a, cudaStream_t s) {
   using PL = FftPlan<N>;
   constexpr int TPC = tiles_per_cta<PL>();
   constexpr int THREADS = TPC * tile_threads<PL>();
-  const size_t smem = (size_t)axis_smem_floats2<PL>() * sizeof(float2);
+  const size_t smem = (size_t)axis_kernel_smem_floats2<PL, INV, AXIS>() * sizeof(float2);
   static SmemOnce once;
   cudaError_t e = raise_smem_limit(axis_fft_kernel<PL, INV, AXIS>, smem, once);
   if (e != cudaSuccess) return e;
