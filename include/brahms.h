@@ -400,6 +400,18 @@ brahms_status brahms_energy_static(const void* const* fields, int nfields, int n
  * launch; waits.  E_ARG for a NULL output, E_CUDA if a launch fails. */
 brahms_status brahms_fp32_fma_rate(void* cuda_stream, double* tflops);
 
+/* Measured all-to-all exchange rate [TB/s] of distributed shared memory
+ * within thread-block clusters of cluster_ctas CTAs (2, 4, 8 or 16), each CTA
+ * holding smem_bytes (1 KB .. 227 KB) of shared memory in cluster_ctas
+ * chunks and storing chunk j into CTA j's shared memory, 200 rounds with a
+ * cluster barrier after each, one resident wave of clusters; the rate counts
+ * the bytes that cross between CTAs.  (The paper has no counterpart: the
+ * measurement that decides whether a step keeping whole (x, y) planes of all
+ * fields on chip, exchanged twice per plane through this memory, can beat
+ * two more HBM passes.)  Waits.  E_SIZE if no cluster of that shape fits,
+ * E_ARG for other sizes, E_CUDA if a launch fails. */
+brahms_status brahms_dsmem_exchange_rate(int cluster_ctas, int smem_bytes, void* cuda_stream, double* tbps);
+
 /* Fault injection for tests of the error paths: the next `count` device or
  * pinned-host allocations the library makes (context workspace and its
  * pinned readback word, adjoint checkpoints, thermal buffers, batch memory)

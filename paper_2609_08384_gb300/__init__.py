@@ -94,6 +94,7 @@ SIGNATURES = {
     "brahms_batch_free": (None, [_vp]),
     "brahms_batch_last_error": (_c.c_char_p, [_vp]),
     "brahms_fp32_fma_rate": (_c.c_int, [_vp, _dp]),
+    "brahms_dsmem_exchange_rate": (_c.c_int, [_c.c_int, _c.c_int, _vp, _dp]),
     "brahms_fail_next_allocations": (_c.c_int, [_c.c_int]),
     "brahms_pending_allocation_failures": (_c.c_int, []),
     "brahms_free": (None, [_vp]),
@@ -487,6 +488,18 @@ def fp32_fma_rate(stream=None) -> float:
     st = stream if stream is not None else torch.cuda.current_stream()
     v = ctypes.c_double()
     _check(None, load().brahms_fp32_fma_rate(_vp(st.cuda_stream), ctypes.byref(v)))
+    return v.value
+
+
+def dsmem_exchange_rate(cluster_ctas: int, smem_bytes: int, stream=None) -> float:
+    """Measured all-to-all exchange rate (TB/s) of distributed shared memory
+    in clusters of cluster_ctas CTAs with smem_bytes each."""
+    import torch
+
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = ctypes.c_double()
+    _check(None, load().brahms_dsmem_exchange_rate(int(cluster_ctas), int(smem_bytes), _vp(st.cuda_stream),
+                                                   ctypes.byref(v)))
     return v.value
 
 
