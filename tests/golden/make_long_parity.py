@@ -99,6 +99,13 @@ def case_opg50():
     return propagate_case("opg50", p, wl.inputs_opg(p), 50, np.full(50, p.dk), 102)
 
 
+def case_opg1000():
+    """The whole OPG workload: 1000 steps of 10 um over 10 mm (about five
+    hours of the oracle on 8 host cores)."""
+    p = wl.problem_opg()
+    return propagate_case("opg1000", p, wl.inputs_opg(p), p.nz, np.full(p.nz, p.dk), 103)
+
+
 def case_batch():
     out, total = {}, 0.0
     for m, (nx, nt, dk, length, nz) in enumerate(BATCH_MEMBERS):
@@ -180,6 +187,7 @@ CASES = {
     # name: (function, approximate cost on 8 x86 cores)
     "sfg_128x128x256_500": (case_sfg, "18 min"),
     "opg_256x256x512_50": (case_opg50, "15 min"),
+    "opg_256x256x512_1000": (case_opg1000, "5 h"),
     "batch_shg_4shapes": (case_batch, "8 min"),
     "adjoint_128x128x256_40": (case_adjoint40, "4 min"),
     "adjoint_128x128x256_400_fd": (case_adjoint400_fd, "60 min"),

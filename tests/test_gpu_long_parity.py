@@ -9,9 +9,8 @@ other inputs fails instead of comparing different problems.
 
 Cases:
   - SFG, 3 x 128x128x256, all 500 steps of 10 um (the SFG workload);
-  - OPG, 3 x 256x256x512, the first 50 of its 1000 steps (routine parity of
-    the full-size workload; the energy invariants of the whole run are in
-    test_gpu_parity.py);
+  - OPG, 3 x 256x256x512, the first 50 of its 1000 steps, and the whole
+    1000-step run;
   - one batched instance of each compiled-in batch shape, 220-640 steps;
   - the adjoint workload's gradient on its full 128x128x256 grid over its
     first 40 steps against the oracle's gradient;
@@ -120,6 +119,18 @@ def test_opg_256x256x512_first_50_steps():
     _check_inputs(d, init)
     got, e, power, _, _ = _run_plain(p, init, 50)
     _compare("opg_256x256x512_50", d, got, e, power)
+
+
+def test_opg_256x256x512_whole_1000_step_run():
+    """The whole OPG workload, 1000 steps over 10 mm, against the oracle's
+    single long host run (its duration is recorded in the file)."""
+    d = _gold("opg_256x256x512_1000")
+    p = wl.problem_opg()
+    init = wl.inputs_opg(p)
+    _check_inputs(d, init)
+    got, e, power, z, phi = _run_plain(p, init, p.nz)
+    assert int(d["nz"]) == p.nz and abs(z - p.length) < 1e-12
+    _compare("opg_256x256x512_1000", d, got, e, power)
 
 
 def test_batched_instances_of_every_shape_over_their_full_runs():

@@ -662,3 +662,52 @@ def test_boyd_kleinman_convergence_in_dz():
     slopes = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
     assert all(1.7 < sl < 2.3 for sl in slopes), (errs, slopes)
     assert to_closed_form[-1] < 1e-4
+
+
+def test_degenerate_cases():
+    """nz = 0 changes nothing (bits and z); zero fields stay exactly zero
+    through the whole split step (both operators map 0 to 0); one step
+    (the first and the last half step in one x-pass pair) and a one-step
+    batched instance match the oracle and the single-instance path."""
+    br = _br()
+    g = wl.Grid(32, 24, 48, 12.5 * wl.UM, 12.5 * wl.UM, 50 * wl.FS)
+    fields = [wl.FieldParams(wl.LAM_P, wl.N_P, delta=1e-10, k2=2e-25, rho=2e-3),
+              wl.FieldParams(wl.LAM_S, wl.N_S, k2=1e-25),
+              wl.FieldParams(wl.LAM_I, wl.N_I, delta=-1e-10, rho=1e-3)]
+    rng = np.random.default_rng(41)
+    init = [_c64(_smooth(g, rng, 3e7)) for _ in range(3)]
+    s = br.Solver(g, fields, wl.D_EFF, 30.0)
+    s.set_fields(_dev(init))
+    s.propagate(0, 10 * wl.UM)
+    assert s.get_z() == (0.0, 0.0)
+    out = s.get_fields()
+    for f in range(3):
+        assert np.array_equal(out[f], init[f])
+    zero = [np.zeros_like(init[0]) for _ in range(3)]
+    s.set_fields(_dev(zero))
+    s.propagate(7, 10 * wl.UM)
+    out = s.get_fields()
+    e, _ = s.energy()
+    for f in range(3):
+        assert not np.any(out[f]) and e[f] == 0.0
+    s.close()
+    got, ref, e_gpu, e_ref = _run_both(g, fields, init, 1, 10 * wl.UM, 30.0)
+    for f in range(3):
+        assert rel_l2(got[f], ref[f]) < FIELD_TOL, f
+    p = wl.problem_batch_member(64, 128, 80.0, 0.01 * wl.MM, 1)
+    inp = wl.inputs_shg(p)
+    for mode in (1, 2):
+        b = br.Batch()
+        b.set_mode(mode)
+        b.set_fields(b.add(p.grid, p.fields, p.d_eff, p.dk, p.nz, p.dz), _dev(inp))
+        b.run()
+        b.sync()
+        o = b.get_fields(0)
+        b.close()
+        sp = br.Solver(p.grid, p.fields, p.d_eff, p.dk)
+        sp.set_fields(_dev(inp))
+        sp.propagate(1, p.dz)
+        want = sp.get_fields()
+        sp.close()
+        for f in range(2):
+            assert rel_l2(o[f], want[f]) < 1e-6, (mode, f)
