@@ -81,6 +81,7 @@ constexpr int batch_smem_floats2() {
 
 struct InstDev {
   float2* state;
+  const float2* ecoef;  // stage factors of every x-pass: [step + 1][6] (see stage_table)
   long long fstride;
   const float4 *twx, *twt;  // NX = NY: one table serves x and y
   const float2 *px, *py, *pt;
@@ -206,7 +207,7 @@ __device__ __noinline__ void run_item(const InstDev& I, const Item& it, float4* 
     }
     float2* coef = reinterpret_cast<float2*>(sm4);
     float2* rowbuf = coef + 12;
-    nl_coefficients<2>(p, coef);
+    if (threadIdx.x < 6) coef[threadIdx.x] = I.ecoef[(it.step + 1) * 6 + threadIdx.x];
     __syncthreads();
     for (long long c = 0; c < it.ntiles; ++c) {
       xpass_tile<NXY, 2, kBT>(p, it.tile + c, coef, rowbuf);
@@ -391,6 +392,7 @@ struct BatchInstHost {
   float2* state = nullptr;
   float4 *twx = nullptr, *twt = nullptr;
   float2 *px = nullptr, *py = nullptr, *pt = nullptr;
+  const float2* ecoef = nullptr;  // its stage factors in its group's table, [step + 1][6]
   bool have_fields = false;
   long long npoints() const { return (long long)nx * ny * nt; }
 };
@@ -407,6 +409,8 @@ struct BatchGroup {
   float2 *px = nullptr, *py = nullptr, *pt = nullptr;
   float4 *twx = nullptr, *twy = nullptr, *twt = nullptr;
   GroupInst* params = nullptr;
+  float2* ecoef = nullptr;  // stage factors [slot][steps + 1][6]
+  int ecoef_steps = 0;      // steps per slot in the table (the group's largest nz)
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   long long npoints() const { return (long long)nx * ny * nt; }
@@ -500,6 +504,41 @@ int effective_nz(const brahms_batch* b, const BatchInstHost& I) {
   return b->nz_cap > 0 ? std::min(I.nz, b->nz_cap) : I.nz;
 }
 
+// The stage factors e^{+i Phi} of every x-pass of every instance of a group,
+// [slot][step + 1][6] (step -1: the first half step), formed on the host in
+// FP64 exactly as the single-instance path forms them: the same phase
+// accumulation Phi_{j+1} = Phi_j + dk dz and the same reduction
+// (fill_stage_factors), so a batched instance computes what
+// brahms_propagate computes, bit for bit.
+cudaError_t stage_table(brahms_batch* b, BatchGroup& g) {
+  const int S = g.ecoef_steps + 1;
+  std::vector<float2> h((size_t)6 * S * g.members.size(), make_float2(1.f, 0.f));
+  for (size_t slot = 0; slot < g.members.size(); ++slot) {
+    const BatchInstHost& I = b->inst[g.members[slot]];
+    XPassArgs x{};
+    x.dz = I.dz;
+    double phi = 0.0;
+    for (int j = -1; j < I.nz; ++j) {
+      if (j < 0) {
+        x.phiB = x.dkB = 0.0;
+        x.phiA = phi;
+        x.dkA = I.dk;
+      } else {
+        x.phiB = phi;
+        x.dkB = I.dk;
+        phi += I.dk * I.dz;
+        x.phiA = phi;
+        x.dkA = I.dk;
+      }
+      fill_stage_factors(x);
+      for (int s = 0; s < 6; ++s) h[((size_t)slot * S + (j + 1)) * 6 + s] = x.ecoef[s];
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g.ecoef, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // h is a local buffer
+  return e;
+}
+
 // Group the instances by shape into arrays of their own (see BatchGroup):
 // the fields move there, the tables are rebuilt there, and every instance's
 // pointers (used by both forms) point into its group.
@@ -542,6 +581,9 @@ brahms_status layout(brahms_batch* b) {
                  o_twx = take(sizeof(float4) * tw_table_size_of(g.nx)),
                  o_twy = take(sizeof(float4) * tw_table_size_of(g.ny)),
                  o_twt = take(sizeof(float4) * tw_table_size_of(g.nt)), o_par = take(sizeof(GroupInst) * m);
+    g.ecoef_steps = 0;
+    for (int i : g.members) g.ecoef_steps = std::max(g.ecoef_steps, b->inst[i].nz);
+    const size_t o_coef = take(sizeof(float2) * 6 * (size_t)(g.ecoef_steps + 1) * m);
     if (dev_alloc((void**)&g.mem, off) != cudaSuccess) {
       cudaGetLastError();
       return release(bfail(b, BRAHMS_E_OOM, "batch group memory"));
@@ -554,12 +596,14 @@ brahms_status layout(brahms_batch* b) {
     g.twy = (float4*)(g.mem + o_twy);
     g.twt = (float4*)(g.mem + o_twt);
     g.params = (GroupInst*)(g.mem + o_par);
+    g.ecoef = (float2*)(g.mem + o_coef);
     if (cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming) != cudaSuccess)
       return release(bfail(b, BRAHMS_E_CUDA, "group stream"));
     cudaError_t e = upload_twiddles(g.twx, g.nx, b->stream);
     if (e == cudaSuccess) e = upload_twiddles(g.twy, g.ny, b->stream);
     if (e == cudaSuccess) e = upload_twiddles(g.twt, g.nt, b->stream);
+    if (e == cudaSuccess) e = stage_table(b, g);
     if (e != cudaSuccess) return release(bfail(b, BRAHMS_E_CUDA, std::string("twiddles: ") + cudaGetErrorString(e)));
     for (size_t slot = 0; slot < m; ++slot) {
       BatchInstHost& I = b->inst[g.members[slot]];
@@ -585,6 +629,7 @@ brahms_status layout(brahms_batch* b) {
       I.pt = g.pt + slot * 2 * g.nt;
       I.twx = g.twx;
       I.twt = g.twt;
+      I.ecoef = g.ecoef + slot * (size_t)(g.ecoef_steps + 1) * 6;
       brahms_status st = build_tables_for(b, I);
       if (st != BRAHMS_OK) {
         b->groups = gs;
@@ -631,7 +676,7 @@ brahms_status prepare_grouped(brahms_batch* b) {
     BB_CK(run_axis_fft(g.ny, 1, true, z, b->stream));
     BB_CK(run_tpass_prop(g.nt, z, b->stream));
     XPassArgs x{};
-    BB_CK(run_xpass_group(g.nx, x, g.params, 0, 0, b->stream));
+    BB_CK(run_xpass_group(g.nx, x, g.params, g.ecoef, 6, 0, 0, b->stream));
     BB_CK(run_xpass(g.nx, 2, x, b->stream));
   }
   cudaStream_t cap = nullptr;
@@ -664,7 +709,7 @@ brahms_status prepare_grouped(brahms_batch* b) {
     // an x-pass over the first a slots (per instance where an instance's rows
     // do not fill whole CTAs)
     auto xpass = [&](int step, int a) -> cudaError_t {
-      if (whole) return run_xpass_group(g.nx, base, g.params, step, a, s);
+      if (whole) return run_xpass_group(g.nx, base, g.params, g.ecoef, (g.ecoef_steps + 1) * 6, step, a, s);
       for (int slot = 0; slot < a; ++slot) {
         const BatchInstHost& I = b->inst[g.members[slot]];
         XPassArgs p = base;
@@ -676,15 +721,18 @@ brahms_status prepare_grouped(brahms_batch* b) {
           p.kh[f] = (float)(k * 0.5 * I.dz);
           p.kh2[f] = 0.5f * p.kh[f];
         }
+        // the phase accumulated as brahms_propagate accumulates it
+        double phi = 0.0;
+        for (int j = 0; j < step; ++j) phi += I.dk * I.dz;
         if (step < 0) {
           p.mode = XM_NL_FIRST;
           p.phiA = 0.0;
           p.dkA = I.dk;
         } else {
           p.mode = step == nzs[slot] - 1 ? XM_NL_LAST : XM_NL_MID;
-          p.phiB = I.dk * (step * I.dz);
+          p.phiB = phi;
           p.dkB = I.dk;
-          p.phiA = I.dk * ((step + 1) * I.dz);
+          p.phiA = phi + I.dk * I.dz;
           p.dkA = I.dk;
         }
         cudaError_t ee = run_xpass(g.nx, 2, p, s);
@@ -776,6 +824,7 @@ brahms_status prepare_persistent(brahms_batch* b) {
     const BatchInstHost& I = b->inst[b->order[r]];
     InstDev& d = h[r];
     d.state = I.state;
+    d.ecoef = I.ecoef;
     d.fstride = I.npoints();
     d.twx = I.twx;
     d.twt = I.twt;

@@ -4,9 +4,10 @@
 // array ([instance][field][tau][y][x]), so instance i's field f starts at
 // (2 i + f) fstride.  Each CTA's rows belong to one instance (the rows of an
 // instance are a whole number of CTA tiles), whose step size, coupling and
-// mismatch come from a per-instance table; the mismatch phase of step j is
-// Phi = dk (j dz) in FP64, the mode (middle or last x-pass of the instance's
-// propagation) follows from its step count.
+// mismatch come from a per-instance table and its stage factors from a table
+// formed on the host as the single-instance path forms them; the mode
+// (middle or last x-pass of the instance's propagation) follows from its
+// step count.
 #include "kernels.cuh"
 #include "launch_cfg.h"
 
@@ -14,7 +15,8 @@ namespace brahms {
 
 template <int NX>
 __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_min_blocks<NX, 2>())
-    xpass_group_kernel(const XPassArgs base, const GroupInst* __restrict__ gi, int step, long long tiles_per_inst) {
+    xpass_group_kernel(const XPassArgs base, const GroupInst* __restrict__ gi, const float2* __restrict__ ecoef,
+                       int stride, int step, long long tiles_per_inst) {
   constexpr int THREADS = xpass_threads<NX>();
   extern __shared__ float4 sm4[];
   float2* coef = reinterpret_cast<float2*>(sm4);
@@ -31,24 +33,15 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_min_blocks<NX, 2>()
   p.kh[1] = g.kh[1];
   p.kh2[0] = g.kh2[0];
   p.kh2[1] = g.kh2[1];
-  if (step < 0) {
-    p.mode = XM_NL_FIRST;
-    p.phiA = 0.0;
-    p.dkA = g.dk;
-  } else {
-    p.mode = step == g.nz - 1 ? XM_NL_LAST : XM_NL_MID;
-    p.phiB = g.dk * (step * g.dz);
-    p.dkB = g.dk;
-    p.phiA = g.dk * ((step + 1) * g.dz);
-    p.dkA = g.dk;
-  }
-  nl_coefficients<2>(p, coef);
+  p.mode = step < 0 ? XM_NL_FIRST : (step == g.nz - 1 ? XM_NL_LAST : XM_NL_MID);
+  if (threadIdx.x < 6) coef[threadIdx.x] = ecoef[(long long)i * stride + (step + 1) * 6 + threadIdx.x];
   __syncthreads();
   xpass_tile<NX, 2, THREADS>(p, lt, coef, rowbuf);
 }
 
 template <int NX>
-static cudaError_t launch_group(const XPassArgs& base, const GroupInst* gi, int step, int ninst, cudaStream_t s) {
+static cudaError_t launch_group(const XPassArgs& base, const GroupInst* gi, const float2* ecoef, int stride, int step,
+                                int ninst, cudaStream_t s) {
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(2) * sizeof(float2);
@@ -59,15 +52,16 @@ static cudaError_t launch_group(const XPassArgs& base, const GroupInst* gi, int 
   const long long tiles = base.rows / ROWS;
   const long long grid = tiles * ninst;
   if (grid <= 0) return cudaSuccess;
-  xpass_group_kernel<NX><<<(unsigned)grid, THREADS, smem, s>>>(base, gi, step, tiles);
+  xpass_group_kernel<NX><<<(unsigned)grid, THREADS, smem, s>>>(base, gi, ecoef, stride, step, tiles);
   return cudaPeekAtLastError();
 }
 
-cudaError_t run_xpass_group(int nx, const XPassArgs& base, const GroupInst* gi, int step, int ninst, cudaStream_t s) {
+cudaError_t run_xpass_group(int nx, const XPassArgs& base, const GroupInst* gi, const float2* ecoef, int stride,
+                            int step, int ninst, cudaStream_t s) {
   switch (nx) {
 #define BRAHMS_G_CASE(N) \
   case N:                \
-    return launch_group<N>(base, gi, step, ninst, s);
+    return launch_group<N>(base, gi, ecoef, stride, step, ninst, s);
     BRAHMS_FOR_EACH_SIZE(BRAHMS_G_CASE)
 #undef BRAHMS_G_CASE
     default:

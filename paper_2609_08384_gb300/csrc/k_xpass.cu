@@ -1,11 +1,24 @@
 // x-pass instantiations and dispatch.
+#include <cmath>
+
 #include "kernels.cuh"
 #include "launch_cfg.h"
 
 namespace brahms {
 
+void fill_stage_factors(XPassArgs& a) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int s = 0; s < 6; ++s) {
+    const double phi = s < 3 ? a.phiB + a.dkB * (0.5 * a.dz + 0.25 * a.dz * s) : a.phiA + a.dkA * (0.25 * a.dz * (s - 3));
+    const double r = phi - two_pi * std::rint(phi / two_pi);
+    a.ecoef[s] = make_float2((float)std::cos(r), (float)std::sin(r));
+  }
+}
+
 template <int NX, int F, bool MAP>
-static cudaError_t launch_x_variant(const XPassArgs& a, cudaStream_t s) {
+static cudaError_t launch_x_variant(const XPassArgs& a0, cudaStream_t s) {
+  XPassArgs a = a0;
+  fill_stage_factors(a);
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);

@@ -45,7 +45,15 @@ struct XPassArgs {
   // enters the B half step and of the state that enters the A half step, or NULL
   float2* rec_b;
   float2* rec_a;
+  // the six stage factors e^{+i Phi} (B half: start, 3/4, end; A half: start,
+  // 1/4, 1/2 of the step) from the phases above, written by the host
+  // dispatchers in FP64 (map-free x-passes read them instead of computing
+  // them per CTA)
+  float2 ecoef[6];
 };
+// Host: the stage factors of an x-pass from its phases (FP64 phase, reduced
+// mod 2 pi, cos and sin in FP64, rounded to float).
+void fill_stage_factors(XPassArgs& a);
 
 struct AxisArgs {
   float2* data;
@@ -385,7 +393,11 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_min_blocks<NX, F>()
   extern __shared__ float4 sm4[];
   float2* coef = reinterpret_cast<float2*>(sm4);
   float2* rowbuf = coef + 6 * F;
-  if constexpr (!MAP) nl_coefficients<F>(p, coef);
+  // stage factors from the launch (formed on the host in FP64: a per-CTA FP64
+  // phase reduction ahead of this barrier stalled every CTA's first warps)
+  if constexpr (!MAP) {
+    if (threadIdx.x < 6) coef[threadIdx.x] = p.ecoef[threadIdx.x];
+  }
   __syncthreads();
   // rows from the last tau-plane down (see the note on pass order above)
   xpass_tile<NX, F, THREADS, MAP, REC>(p, (long long)gridDim.x - 1 - blockIdx.x, coef, rowbuf);
@@ -562,7 +574,10 @@ struct GroupInst {
   double dk, dz;
   int nz;
 };
-cudaError_t run_xpass_group(int nx, const XPassArgs& base, const GroupInst* gi, int step, int ninst, cudaStream_t s);
+// ecoef: the instances' stage factors, instance i's for step j at
+// ecoef[i stride + (j + 1) 6 + 0..5]
+cudaError_t run_xpass_group(int nx, const XPassArgs& base, const GroupInst* gi, const float2* ecoef, int stride,
+                            int step, int ninst, cudaStream_t s);
 int xpass_rows_of(int nx);  // rows per CTA of the x-pass of length nx
 
 // misc kernels (k_misc.cu)

@@ -9,7 +9,9 @@
 namespace brahms {
 
 template <int NX, int F, bool MAP>
-cudaError_t launch_record(const XPassArgs& a, cudaStream_t s) {
+cudaError_t launch_record(const XPassArgs& a0, cudaStream_t s) {
+  XPassArgs a = a0;
+  fill_stage_factors(a);
   constexpr int ROWS = xpass_rows<NX>();
   constexpr int THREADS = xpass_threads<NX>();
   const size_t smem = (size_t)xpass_smem_floats2<NX>(F) * sizeof(float2);

@@ -88,6 +88,19 @@ def test_batch_matches_single_instance_and_oracle(mode):
             assert rel_l2(o[f], ref[f]) < 1e-4, (p.name, f)
 
 
+def test_grouped_form_is_bit_identical_to_the_single_instance_path():
+    """The grouped form runs the single-instance kernels on the same tables
+    with the same stage factors (formed on the host with the same phase
+    accumulation), so every instance gives brahms_propagate's bits."""
+    probs = _mixed_problems(seed=9)
+    inputs = [wl.inputs_shg(p) for p in probs]
+    out, _, _ = _run_batch(probs, inputs, mode=GROUPED)
+    for p, inp, o in zip(probs, inputs, out):
+        ref = _plain(p, inp)
+        for f in range(2):
+            assert np.array_equal(o[f], ref[f]), (p.name, f)
+
+
 def test_grouped_and_persistent_forms_agree():
     """The two forms run the same kernel code on the same tables: the results
     agree bit for bit (up to the FP64 phase bookkeeping, which both share)."""
