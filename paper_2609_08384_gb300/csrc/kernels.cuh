@@ -493,8 +493,10 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
   // now v[b RL + r] = A_hat(kx, ky, Omega_k), k = t + b T + r N/RL.
   // P = (1 + Dx)(1 + Dy)(1 + Dt) applied as w + w D with w = v/(nx ny nt).
   // (Measured slower on the 512-point plan: w (1 + Dt)(1 + Dxy) as two
-  // delta-form products, 127 registers and 522 us against 104 and 476; and
-  // the scale and conjugation as four specialised copies, 542 us.)
+  // delta-form products, 127 registers and 522 us against 104 and 476; the
+  // scale and conjugation as four specialised copies, 542 us; the twiddle
+  // staging issued after this tile's loads instead of before them, 520 us;
+  // a persistent loop over tiles, 542 us.)
   float2 dxy = make_float2(0.f, 0.f);
   if (a.act) {
     const float2 dx = p.px[a.f * p.nx + a.x], dy = p.py[a.f * p.ny + a.other];
