@@ -1,6 +1,8 @@
 // The reverse x-pass of the adjoint (kernel in xadj.cuh): map-free
 // instantiations, dispatch, and the fixed-order reduction of the per-CTA
 // stage-phase sensitivities.
+#include <cmath>
+
 #include "xadj.cuh"
 
 namespace brahms {
@@ -31,8 +33,28 @@ __global__ void __launch_bounds__(256) sens_boundary_kernel(const double* __rest
 }
 
 
-cudaError_t run_xpass_adjoint(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s) {
-  if (a.emap) return run_xpass_adjoint_map(nx, nf, a, ncta, s);
+// i kappa_f h e^{-/+ i Phi} at the start, middle and end of a half step that
+// starts at phase phi_a with mismatch dk: the phase in FP64, reduced mod 2 pi,
+// cos and sin in FP64 rounded to float (the forward x-pass's stage factors),
+// the products with kappa_f h in float as the device forms them
+static void coef_sets(double phi_a, double dk, double h, const float* kh, int nf, float2* c) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int s = 0; s < 3; ++s) {
+    const double phi = phi_a + dk * (0.5 * h * s);
+    const double r = phi - two_pi * std::rint(phi / two_pi);
+    const float2 em = make_float2((float)std::cos(r), -(float)std::sin(r));  // e^{-i Phi}
+    for (int f = 0; f < nf; ++f) {
+      const float k = kh[f];
+      c[s * nf + f] = f == 0 ? make_float2(-em.y * k, em.x * k) : make_float2(em.y * k, em.x * k);
+    }
+  }
+}
+
+cudaError_t run_xpass_adjoint(int nx, int nf, const XAdjArgs& a0, long long* ncta, cudaStream_t s) {
+  if (a0.emap) return run_xpass_adjoint_map(nx, nf, a0, ncta, s);
+  XAdjArgs a = a0;
+  coef_sets(a.phiA, a.dkA, a.h, a.kh, nf, a.cset[0]);
+  coef_sets(a.phiB, a.dkB, a.h, a.kh, nf, a.cset[1]);
   switch (nx) {
 #define BRAHMS_XA_CASE(N) \
   case N:                 \

@@ -678,6 +678,11 @@ struct XAdjArgs {
   // boundary's B and A half steps [4][ny][nx] (as in XPassArgs), or NULL
   const float2* emap;
   int ny;
+  // map-free: the coefficient sets i kappa_f h e^{-/+ i Phi} at the start,
+  // middle and end of the A half step (cset[0]) and of the B half step
+  // (cset[1]), [stage][field], written by the host dispatcher in FP64 from
+  // the phases above (the stage factors the forward x-pass uses)
+  float2 cset[2][9];
 };
 cudaError_t run_xpass_adjoint(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s);
 cudaError_t run_xpass_adjoint_map(int nx, int nf, const XAdjArgs& a, long long* ncta, cudaStream_t s);

@@ -166,8 +166,11 @@ __global__ void __launch_bounds__(xpass_threads<NX>(), xpass_threads<NX>() <= 12
   float2* rowbuf = cA + 6 * F;
   __shared__ double red[THREADS / 32][6];
   if constexpr (!MAP) {
-    vjp_coef_sets<F>(p.phiA, p.dkA, p.h, p.kh, cA);
-    vjp_coef_sets<F>(p.phiB, p.dkB, p.h, p.kh, cB);
+    // coefficient sets from the launch (formed on the host in FP64)
+    if (threadIdx.x < 3 * F) {
+      cA[threadIdx.x] = p.cset[0][threadIdx.x];
+      cB[threadIdx.x] = p.cset[1][threadIdx.x];
+    }
   }
   __syncthreads();
   float sens[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
