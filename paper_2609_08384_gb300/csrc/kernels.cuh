@@ -496,7 +496,9 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
   // delta-form products, 127 registers and 522 us against 104 and 476; the
   // scale and conjugation as four specialised copies, 542 us; the twiddle
   // staging issued after this tile's loads instead of before them, 520 us;
-  // a persistent loop over tiles, 542 us.)
+  // a persistent loop over tiles, 542 us; the first pass's loads issued in
+  // the order the radix-32 codelet consumes them, 549 us; launch bounds of
+  // two CTAs per SM (128 registers), 531 us.)
   float2 dxy = make_float2(0.f, 0.f);
   if (a.act) {
     const float2 dx = p.px[a.f * p.nx + a.x], dy = p.py[a.f * p.ny + a.other];
