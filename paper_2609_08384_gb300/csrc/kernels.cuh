@@ -420,7 +420,9 @@ __device__ __forceinline__ float2 mul_one_plus(float2 w, float2 d) { return cadd
 // still in L2 (read there, and overwritten there before they are written
 // back).  Measured on the 3 x 256x256x512 state: 1603 -> 1592 ms per
 // 1000-step call; a tau-major y order (every field of a plane together)
-// made the y-passes 20 us slower and the step 1622 ms.
+// made the y-passes 20 us slower and the step 1622 ms.  The tau-propagator
+// also walks its tiles from the last down (tau 476 -> 473, y-inverse
+// 258 -> 257 us).
 template <int N, int AXIS, int TX>
 struct AxisTile {
   float2* base;  // element (x, pencil index 0)
@@ -553,7 +555,10 @@ __global__ void __launch_bounds__(tiles_per_cta<PL>() * tile_threads<PL>())
     float4* tw = sm4;
     for (int i = threadIdx.x; i < tw_table_size<PL>(); i += blockDim.x) tw[i] = p.tw[i];
     __syncthreads();
-    tprop_tile<PL, THREADS>(p, blockIdx.x, TwShared{tw}, reinterpret_cast<float2*>(tw + tw_table_size<PL>()));
+    // tiles from the last down: the pass ends on the first field's low-y
+    // pencils, which the y-inverse then reads first
+    tprop_tile<PL, THREADS>(p, (long long)gridDim.x - 1 - blockIdx.x, TwShared{tw},
+                            reinterpret_cast<float2*>(tw + tw_table_size<PL>()));
   } else {
     tprop_tile<PL, THREADS>(p, blockIdx.x, TwGlobal{p.tw}, reinterpret_cast<float2*>(sm4));
   }
