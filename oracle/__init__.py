@@ -26,6 +26,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                       sensitivities and full gradients against central
                       finite differences of objective(), with and without
                       a transverse mismatch map
+  propagate_map_z     piecewise-constant mismatch per column against the
+                      undepleted closed form sum_s e^{-i Phi(z_s)} (1 -
+                      e^{-i dk_s l_s}) / (i dk_s); uniform segments equal the
+                      per-step profile, one segment equals propagate_map
   spectral_phase      a linear phase Omega m dt is an exact circular shift
                       by m samples (both signs, 1e-13); a quadratic phase on a
                       Gaussian gives the chirped-Gaussian closed form (1e-9)
@@ -100,6 +104,9 @@ def _load():
             lib.orc_propagate_map.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp,
                                               ctypes.c_double, dp]
             lib.orc_propagate_map.restype = ctypes.c_int
+            lib.orc_propagate_map_z.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int,
+                                                dp, dp]
+            lib.orc_propagate_map_z.restype = ctypes.c_int
             lib.orc_power_trace.argtypes = [P(_Problem), vp, dp]
             lib.orc_spectrum.argtypes = [P(_Problem), vp, dp]
             lib.orc_heat_load.argtypes = [P(_Problem), vp, ctypes.c_double, dp]
@@ -224,6 +231,31 @@ def propagate_map(prob: _Problem, fields: Sequence[np.ndarray], nz: int, dz: flo
     dp = ctypes.POINTER(ctypes.c_double)
     rc = _load().orc_propagate_map(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), dks.ctypes.data_as(dp),
                                    ctypes.byref(phi), float(z0), m.ctypes.data_as(dp))
+    if check and rc != 0:
+        raise FloatingPointError("oracle: non-finite fields (dz too large)")
+    return a, phi.value
+
+
+def propagate_map_z(prob: _Problem, fields: Sequence[np.ndarray], nz: int, dz: float, dk, z_edges,
+                    maps: np.ndarray, phi0: float = 0.0, check: bool = True):
+    """propagate() from z = 0 under a mismatch map that changes along z:
+    maps[s, ny, nx] [1/m] on the segments separated by the increasing
+    distances z_edges (len(maps) - 1 of them); step j takes the segment of
+    its midpoint, and the coupling phase is the integral of the mismatch
+    (orc_propagate_map_z)."""
+    a = _stack(fields)
+    dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
+    m = np.ascontiguousarray(maps, dtype=np.float64).reshape(-1, prob.ny, prob.nx)
+    e = np.ascontiguousarray(np.asarray(z_edges, dtype=np.float64).reshape(-1))
+    if len(e) != len(m) - 1 or np.any(np.diff(e) <= 0):
+        raise ValueError("need len(maps) - 1 increasing z_edges")
+    e = e if len(e) else np.zeros(1)
+    phi = ctypes.c_double(phi0)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = _load().orc_propagate_map_z(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), dks.ctypes.data_as(dp),
+                                     ctypes.byref(phi), int(len(m)), e.ctypes.data_as(dp), m.ctypes.data_as(dp))
+    if rc == 1:
+        raise MemoryError("oracle: map phase buffers")
     if check and rc != 0:
         raise FloatingPointError("oracle: non-finite fields (dz too large)")
     return a, phi.value

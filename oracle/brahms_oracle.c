@@ -404,6 +404,48 @@ void orc_nonlinear_step_map(const orc_problem* pb, cplx* fields, double phi_a, d
   parallel_for((int64_t)pb->nx * pb->ny * pb->nt, nlm_range, &j);
 }
 
+/* N(h) with a per-point phase origin: at every point
+ *   Phi(x, y, z_a + s) = phi_a + q(x, y) + (dk + dk_map(x, y)) s,
+ * q[y nx + x] the integral of the map over the distance already travelled
+ * (used when the map changes along z; orc_nonlinear_step_map is the case
+ * q = dk_map z_a).                                                         */
+typedef struct {
+  const orc_problem* pb;
+  cplx* fields;
+  double kap[3];
+  double phi_a, dk, h;
+  const double* q;
+  const double* dk_map;
+} nlq_job;
+
+static void nlq_range(void* p, int64_t b, int64_t e) {
+  nlq_job* j = (nlq_job*)p;
+  const int64_t plane = (int64_t)j->pb->nx * j->pb->ny;
+  const int64_t n = plane * j->pb->nt;
+  const int nf = j->pb->nf;
+  for (int64_t i = b; i < e; ++i) {
+    const int64_t xy = i % plane;
+    cplx A[3];
+    for (int f = 0; f < nf; ++f) A[f] = j->fields[f * n + i];
+    orc_rk4_point(nf, j->kap, j->phi_a + j->q[xy], j->dk + j->dk_map[xy], j->h, A);
+    for (int f = 0; f < nf; ++f) j->fields[f * n + i] = A[f];
+  }
+}
+
+static void nonlinear_step_q(const orc_problem* pb, cplx* fields, double phi_a, double dk, double h, const double* q,
+                             const double* dk_map) {
+  nlq_job j;
+  j.pb = pb;
+  j.fields = fields;
+  for (int f = 0; f < pb->nf; ++f) j.kap[f] = orc_kappa(pb, f);
+  j.phi_a = phi_a;
+  j.dk = dk;
+  j.h = h;
+  j.q = q;
+  j.dk_map = dk_map;
+  parallel_for((int64_t)pb->nx * pb->ny * pb->nt, nlq_range, &j);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Split-step propagation (Eq. expon):  N(dz/2)  L(dz)  N(dz/2)  per step.     */
 /* ------------------------------------------------------------------------ */
@@ -440,6 +482,46 @@ int orc_propagate_map(const orc_problem* pb, cplx* fields, int nz, double dz, co
     orc_nonlinear_step_map(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz, zj + 0.5 * dz, dk_map);
     ph += dk * dz;
   }
+  *phi = ph;
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt * pb->nf;
+  for (int64_t i = 0; i < n; ++i)
+    if (!isfinite(creal(fields[i])) || !isfinite(cimag(fields[i]))) return 5;
+  return 0;
+}
+
+/* A mismatch map that changes along z (a z-resolved thermal load, say):
+ * Delta k(x, y, z) = dk_steps[j] + maps[s][y nx + x] on step j, s the segment
+ * that holds the step's midpoint z_j + dz/2, segments separated by the
+ * nseg - 1 increasing distances z_edges (from the start of the crystal).
+ * The coupling phase is the integral of the mismatch from z = 0,
+ *   Phi(x, y, z) = phi(z) + Q(x, y, z),  Q = int_0^z maps[s(z')](x, y) dz',
+ * so it stays continuous where the map changes.  Starts at z = 0 with the
+ * scalar phase *phi (advanced to its value at the end).                     */
+int orc_propagate_map_z(const orc_problem* pb, cplx* fields, int nz, double dz, const double* dk_steps, double* phi,
+                        int nseg, const double* z_edges, const double* maps) {
+  const int64_t plane = (int64_t)pb->nx * pb->ny;
+  double* q = (double*)calloc((size_t)plane, sizeof(double));
+  double* qh = (double*)malloc(sizeof(double) * (size_t)plane);
+  if (!q || !qh) {
+    free(q);
+    free(qh);
+    return 1;
+  }
+  double ph = *phi;
+  for (int j = 0; j < nz; ++j) {
+    const double dk = dk_steps[j], zmid = (j + 0.5) * dz;
+    int s = 0;
+    while (s < nseg - 1 && z_edges[s] <= zmid) ++s;
+    const double* m = maps + (int64_t)s * plane;
+    nonlinear_step_q(pb, fields, ph, dk, 0.5 * dz, q, m);
+    orc_linear_step(pb, fields, dz);
+    for (int64_t i = 0; i < plane; ++i) qh[i] = q[i] + m[i] * (0.5 * dz);
+    nonlinear_step_q(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz, qh, m);
+    for (int64_t i = 0; i < plane; ++i) q[i] += m[i] * dz;
+    ph += dk * dz;
+  }
+  free(q);
+  free(qh);
   *phi = ph;
   int64_t n = (int64_t)pb->nx * pb->ny * pb->nt * pb->nf;
   for (int64_t i = 0; i < n; ++i)

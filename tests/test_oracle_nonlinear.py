@@ -272,3 +272,80 @@ def test_map_split_calls_equal_one_call():
     a, ph = oracle.propagate_map(prob, init, 5, 6 * UM, 80.0, m)
     two, _ = oracle.propagate_map(prob, list(a), 7, 6 * UM, 80.0, m, phi0=ph, z0=5 * 6 * UM)
     assert np.linalg.norm(two - one) / np.linalg.norm(one) < 1e-13
+
+
+# ------------------------------------------- mismatch map changing along z
+def _piecewise_sinc(a, kSH, dks, lengths):
+    """Undepleted SHG under a mismatch that is dks[s] over lengths[s]:
+    A_SH(L) = i (kSH / 2) a^2 int_0^L e^{-i Phi(z)} dz with Phi the integral
+    of the mismatch, summed segment by segment in closed form."""
+    acc, phi = 0.0j, 0.0
+    for d, ell in zip(dks, lengths):
+        seg = ell if d == 0 else (1 - np.exp(-1j * d * ell)) / (1j * d)
+        acc += np.exp(-1j * phi) * seg
+        phi += d * ell
+    return 1j * (kSH / 2) * a * a * acc
+
+
+def test_map_z_columns_follow_piecewise_closed_form():
+    """A fan-out map that changes at two distances: every column follows the
+    undepleted plane-wave law of its own piecewise-constant mismatch, with
+    the phase continuous at the changes (a phase that restarted, or jumped to
+    the new map times z, misses the closed form by O(1))."""
+    g = Grid(8, 2, 2, 1.0, 1.0, 10 * FS)
+    prob = oracle.make_problem(g, _no_walkoff_shg(), D_EFF)
+    kSH = 2 * math.pi * D_EFF / (N_SH * LAM_SH)
+    a = 1.0 + 0.5j
+    L, nz, dk = 3 * MM, 300, 150.0
+    edges = [1.0 * MM, 2.2 * MM]                     # step boundaries 100 and 220
+    ramps = [np.linspace(-2000.0, 2000.0, 8), np.linspace(1500.0, -900.0, 8), np.linspace(-300.0, 2500.0, 8)]
+    maps = np.stack([np.tile(r, (2, 1)) for r in ramps])
+    out, _ = oracle.propagate_map_z(prob, [_uniform(g, 0), _uniform(g, a)], nz, L / nz, dk, edges, maps)
+    lengths = [edges[0], edges[1] - edges[0], L - edges[1]]
+    for x in range(8):
+        expect = _piecewise_sinc(a, kSH, [dk + r[x] for r in ramps], lengths)
+        assert abs(out[0, 1, 1, x] - expect) / abs(kSH * a * a * L) < 1e-9, x
+    # the phase (dk + map in effect at z) * z, which jumps at each change: far off
+    bounds = [0.0, edges[0], edges[1], L]
+    for x in range(8):
+        jump = sum((np.exp(-1j * d * z0) - np.exp(-1j * d * z1)) / (1j * d)
+                   for d, z0, z1 in zip([dk + r[x] for r in ramps], bounds[:-1], bounds[1:]))
+        assert abs(out[0, 1, 1, x] - 1j * (kSH / 2) * a * a * jump) / abs(kSH * a * a * L) > 1e-2, x
+
+
+def test_map_z_uniform_segments_equal_step_profile():
+    """Maps uniform in (x, y) on each segment are a per-step mismatch profile:
+    step j gets dk_j plus its segment's value (segment of the midpoint)."""
+    g = Grid(8, 6, 12, 5 * UM, 5 * UM, 30 * FS)
+    fields = [FieldParams(1064e-9, 2.15, delta=1e-10, k2=2e-25, rho=2e-3),
+              FieldParams(1450e-9, 2.14, k2=1e-25),
+              FieldParams(1.0 / (1.0 / 1064e-9 - 1.0 / 1450e-9), 2.08, delta=-1e-10, rho=1e-3)]
+    prob = oracle.make_problem(g, fields, D_EFF)
+    rng = np.random.default_rng(23)
+    init = [3e8 * (rng.standard_normal((12, 6, 8)) + 1j * rng.standard_normal((12, 6, 8))) for _ in range(3)]
+    nz, dz = 14, 7 * UM
+    prof = rng.normal(0.0, 300.0, nz)
+    edges = [3.2 * dz, 9.6 * dz]                     # midpoints 3.5 dz and 9.5 dz fall on either side
+    vals = [450.0, -800.0, 1200.0]
+    maps = np.stack([np.full((6, 8), v) for v in vals])
+    seg = np.searchsorted(edges, (np.arange(nz) + 0.5) * dz, side="right")
+    assert list(np.bincount(seg)) == [3, 7, 4]
+    ref, phr = oracle.propagate(prob, init, nz, dz, prof + np.take(vals, seg))
+    got, phg = oracle.propagate_map_z(prob, init, nz, dz, prof, edges, maps)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-12
+    assert phg == pytest.approx(phr - float(np.sum(np.take(vals, seg))) * dz, rel=1e-12)
+
+
+def test_map_z_one_segment_equals_static_map():
+    """One segment, or several segments holding the same map, is the static
+    map of propagate_map (per-point indexing of the accumulated phase)."""
+    g = Grid(8, 4, 8, 5 * UM, 5 * UM, 30 * FS)
+    prob = oracle.make_problem(g, _no_walkoff_shg(), D_EFF)
+    rng = np.random.default_rng(29)
+    init = [1e8 * (rng.standard_normal((8, 4, 8)) + 1j * rng.standard_normal((8, 4, 8))) for _ in range(2)]
+    m = rng.normal(0.0, 500.0, (4, 8))
+    ref, _ = oracle.propagate_map(prob, init, 12, 6 * UM, 80.0, m)
+    one, _ = oracle.propagate_map_z(prob, init, 12, 6 * UM, 80.0, [], m[None])
+    three, _ = oracle.propagate_map_z(prob, init, 12, 6 * UM, 80.0, [20 * UM, 41 * UM], np.stack([m, m, m]))
+    assert np.linalg.norm(one - ref) / np.linalg.norm(ref) < 1e-13
+    assert np.linalg.norm(three - ref) / np.linalg.norm(ref) < 1e-13
