@@ -117,12 +117,32 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction);
 
 /* Transverse mismatch map (the mismatch field of a fan-out grating or of a
  * static dephasing profile): dk_map[ny][nx] in 1/m, x fastest, is added to
- * every step's Delta k, so the nonlinear step's phase becomes
- *   Phi(x, y, z) = Phi_j + Delta k_j (z - z_j) + dk_map(x, y) z,
- * z measured from the last brahms_set_fields.  The library copies the map;
- * NULL removes it.  E_ARG for non-finite entries.  The adjoint propagates
- * and differentiates under the map (the map itself is not a parameter). */
+ * every step's Delta k.  The coupling phase is the integral of the mismatch
+ * from the last brahms_set_fields (z = 0):
+ *   Phi(x, y, z) = Phi_j + Delta k_j (z - z_j) + int_0^z dk_map(x, y, z') dz',
+ * which for a map set before the run is Phi_j + Delta k_j (z - z_j) +
+ * dk_map(x, y) z.  A map set between brahms_propagate calls applies from the
+ * current z on, and the phase stays continuous there.  The library copies
+ * the map; NULL removes it (and any z-segments, below).  E_ARG for non-finite
+ * entries.  The adjoint propagates and differentiates under the map (the map
+ * itself is not a parameter). */
 brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
+
+/* A mismatch map that changes along z (e.g. the temperature of a crystal
+ * whose heat load varies along the beam, Sec. 4.1): nseg >= 1 segments
+ * separated by the nseg - 1 distances z_edges [m] from z = 0 (finite,
+ * positive, increasing; NULL when nseg == 1), maps[nseg][ny][nx] in 1/m.
+ * Step j (from z_j to z_j + dz) takes the map of the segment that holds its
+ * midpoint z_j + dz/2, so a segment edge acts at the step boundary nearest
+ * to it; the phase is the integral above, continuous at every edge.  maps ==
+ * NULL sets the segments with zero maps (the segments of the thermal model
+ * alone).  The segmentation also divides the thermal model's heat load
+ * (below); a change of segments drops the loads accumulated so far.  nseg == 1
+ * is brahms_set_dk_map.  E_ARG for nseg outside 1..4096, bad edges or
+ * non-finite maps; E_OOM if the segment maps (2 nseg ny nx doubles) cannot be
+ * allocated.  The adjoint refuses a context with more than one segment
+ * (E_STATE). */
+brahms_status brahms_set_dk_map_z(brahms_ctx* ctx, int nseg, const double* z_edges, const double* maps);
 
 /* Diagnostics of the current fields (the Sec. 6 power formula resolved in
  * tau or Omega); the state is not modified.  Each output holds nfields * nt
@@ -137,41 +157,52 @@ brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectru
 
 /* Thermal model (Sec. 4.1: the steady-state heat equation lap T = -Q / kappa
  * solved on the fields' grid, and the temperature dependence of the phase
- * mismatch).  Three calls:
+ * mismatch).  The heat load is kept per z-segment of the context (one
+ * segment unless brahms_set_dk_map_z set several).  Four calls:
  *
- * brahms_heat_accumulate adds weight * Q(x, y) of the current fields to the
- * context's heat load [W/m^3], Q the absorbed optical power density
+ * brahms_heat_accumulate_segment adds weight * Q(x, y) of the current fields
+ * to segment's heat load [W/m^3], Q the absorbed optical power density
  *   Q = sum_f alpha_f I_f,  I_f = 1/2 c eps0 n_f |A_f|^2,
  * alpha_f the intensity absorption of field f (its brahms_field_params
  * alpha, the same loss the linear step applies).  For nt > 1 the pulses are
  * time-averaged: Q = rep_rate * sum_f alpha_f sum_tau I_f dt (rep_rate in Hz,
  * >= 0); for nt == 1 (cw) rep_rate is ignored.  Sampling the fields at
- * several z and choosing the weights of a quadrature rule (summing to one)
- * gives the z-averaged load.  Asynchronous; FP64 accumulation.
- * E_STATE without fields, E_ARG for a negative rep_rate or non-finite
- * arguments.
+ * several z within a segment and choosing the weights of a quadrature rule
+ * (summing to one) gives the segment's z-averaged load.  Asynchronous; FP64
+ * accumulation.  E_STATE without fields, E_ARG for a segment outside
+ * 0..nseg-1, a negative rep_rate or non-finite arguments.
+ * brahms_heat_accumulate adds to the segment that holds the current
+ * distance z (the segment that starts at z when z is on an edge).
  *
- * brahms_heat_set replaces the load with q[ny][nx] (host, W/m^3, x fastest;
- * any finite values, negative ones being heat sinks); NULL zeroes it.
+ * brahms_heat_set replaces the loads with q[nseg][ny][nx] (host, W/m^3,
+ * x fastest; any finite values, negative ones being heat sinks); NULL zeroes
+ * them.
  *
- * brahms_thermal_map solves, in FP64, the transverse heat equation
- *   -kappa_th (d_xx + d_yy) T = Q
+ * brahms_thermal_map solves, in FP64, for every segment the transverse heat
+ * equation
+ *   -kappa_th (d_xx + d_yy) T_s = Q_s
  * with the 5-point stencil on the fields' (x, y) grid and T = 0 (the mount
  * temperature) half a cell outside the window on every side, i.e. on the
- * crystal's side faces at x_{-1/2} and x_{nx-1/2}; with insulated end faces
- * this is the equation of the z-averaged temperature rise under the
- * z-averaged load.  An axis of length 1 is invariant (no derivative along
- * it).  The solve is direct (sine-transform diagonalisation).  It installs
- * dk_map = M + dkdT * T as the transverse mismatch map, M the map last given
- * to brahms_set_dk_map (a fan-out grating, say; zero if none); a later
+ * crystal's side faces at x_{-1/2} and x_{nx-1/2}.  With insulated end faces
+ * and one segment this is the equation of the z-averaged temperature rise
+ * under the z-averaged load; with several, each segment's temperature under
+ * its own load, heat flow along z between segments neglected (a load that
+ * changes along z over lengths well above the beam width).  An axis of length
+ * 1 is invariant (no derivative along it).  The solve is direct
+ * (sine-transform diagonalisation).  It installs dk_map_s = M_s + dkdT * T_s
+ * as the mismatch map of segment s, M_s the map last given to
+ * brahms_set_dk_map or brahms_set_dk_map_z (a fan-out grating, say; zero if
+ * none), from the current z on (the phase stays continuous); a later
  * brahms_set_dk_map replaces both terms, brahms_set_dk_map(ctx, NULL)
- * removes them.  If temperature is not NULL, it copies T [K above the
- * mount, ny*nx doubles, x fastest] to it.  kappa_th [W/(m K)] must be > 0, dkdT [1/(m K)] finite.
- * E_STATE if no load was accumulated or set.  E_NONFINITE if the load or
- * the temperature is not finite: the thermal map is then not installed and
- * the map in effect becomes the map of brahms_set_dk_map (none if none).
- * Waits for the stream. */
+ * removes them.  If temperature is not NULL, it copies T [K above the mount,
+ * nseg*ny*nx doubles, x fastest] to it.  kappa_th [W/(m K)] must be > 0,
+ * dkdT [1/(m K)] finite.  E_STATE if a segment has no load accumulated or
+ * set.  E_NONFINITE if a load or a temperature is not finite: the thermal
+ * maps are then not installed and the maps in effect become those of
+ * brahms_set_dk_map / brahms_set_dk_map_z (none if none).  Waits for the
+ * stream. */
 brahms_status brahms_heat_accumulate(brahms_ctx* ctx, double rep_rate, double weight);
+brahms_status brahms_heat_accumulate_segment(brahms_ctx* ctx, int segment, double rep_rate, double weight);
 brahms_status brahms_heat_set(brahms_ctx* ctx, const double* q);
 brahms_status brahms_thermal_map(brahms_ctx* ctx, double kappa_th, double dkdT, double* temperature);
 

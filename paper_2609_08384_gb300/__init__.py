@@ -61,7 +61,9 @@ SIGNATURES = {
     "brahms_get_z": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_diagnostics": (_c.c_int, [_vp, _dp, _dp]),
     "brahms_set_dk_map": (_c.c_int, [_vp, _dp]),
+    "brahms_set_dk_map_z": (_c.c_int, [_vp, _c.c_int, _dp, _dp]),
     "brahms_heat_accumulate": (_c.c_int, [_vp, _c.c_double, _c.c_double]),
+    "brahms_heat_accumulate_segment": (_c.c_int, [_vp, _c.c_int, _c.c_double, _c.c_double]),
     "brahms_heat_set": (_c.c_int, [_vp, _dp]),
     "brahms_thermal_map": (_c.c_int, [_vp, _c.c_double, _c.c_double, _dp]),
     "brahms_timing": (_c.c_int, [_vp, _c.c_int, _dp, _llp, _c.c_int]),
@@ -168,6 +170,7 @@ class Solver:
 
         lib = load()
         self.nf = len(fields)
+        self.nseg = 1  # z-segments of the mismatch map and heat load
         self.grid = grid
         self.shape = (grid.nt, grid.ny, grid.nx)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
@@ -231,12 +234,28 @@ class Solver:
         return e, ph
 
     def set_dk_map(self, dk_map):
-        """Transverse mismatch map [ny, nx] in 1/m added to every step's dk; None removes it."""
+        """Transverse mismatch map [ny, nx] in 1/m added to every step's dk from
+        the current z on (the phase is its integral); None removes it."""
         if dk_map is None:
             _check(self.ctx, load().brahms_set_dk_map(self.ctx, None))
-            return
-        m = np.ascontiguousarray(dk_map, dtype=np.float64).reshape(self.grid.ny, self.grid.nx)
-        _check(self.ctx, load().brahms_set_dk_map(self.ctx, m.ctypes.data_as(_dp)))
+        else:
+            m = np.ascontiguousarray(dk_map, dtype=np.float64).reshape(self.grid.ny, self.grid.nx)
+            _check(self.ctx, load().brahms_set_dk_map(self.ctx, m.ctypes.data_as(_dp)))
+        self.nseg = 1
+
+    def set_dk_map_z(self, z_edges, maps=None):
+        """Mismatch maps that change along z: maps [nseg, ny, nx] in 1/m on the
+        segments separated by the nseg - 1 distances z_edges [m] (step j takes
+        the segment of its midpoint); maps None: zero maps (segments of the
+        thermal model alone, nseg = len(z_edges) + 1)."""
+        e = np.ascontiguousarray(np.asarray(z_edges, dtype=np.float64).reshape(-1))
+        nseg = len(e) + 1
+        m = None
+        if maps is not None:
+            m = np.ascontiguousarray(maps, dtype=np.float64).reshape(nseg, self.grid.ny, self.grid.nx)
+        _check(self.ctx, load().brahms_set_dk_map_z(self.ctx, nseg, e.ctypes.data_as(_dp) if len(e) else None,
+                                                    None if m is None else m.ctypes.data_as(_dp)))
+        self.nseg = nseg
 
     def diagnostics(self):
         """(power [nf, nt] in W, spectrum [nf, nt] in J per Omega bin, FFT order)."""
@@ -245,26 +264,33 @@ class Solver:
         _check(self.ctx, load().brahms_diagnostics(self.ctx, p.ctypes.data_as(_dp), sp.ctypes.data_as(_dp)))
         return p, sp
 
-    def heat_accumulate(self, rep_rate: float = 0.0, weight: float = 1.0):
-        """Add weight * Q(x, y) of the current fields to the heat load [W/m^3]
-        (Q = sum_f alpha_f I_f, time-averaged at rep_rate [Hz] when nt > 1)."""
-        _check(self.ctx, load().brahms_heat_accumulate(self.ctx, float(rep_rate), float(weight)))
+    def heat_accumulate(self, rep_rate: float = 0.0, weight: float = 1.0, segment=None):
+        """Add weight * Q(x, y) of the current fields to a z-segment's heat load
+        [W/m^3] (Q = sum_f alpha_f I_f, time-averaged at rep_rate [Hz] when
+        nt > 1); segment None: the segment that holds the current z."""
+        if segment is None:
+            _check(self.ctx, load().brahms_heat_accumulate(self.ctx, float(rep_rate), float(weight)))
+        else:
+            _check(self.ctx, load().brahms_heat_accumulate_segment(self.ctx, int(segment), float(rep_rate),
+                                                                   float(weight)))
 
     def heat_set(self, q):
-        """Replace the heat load with q [ny, nx] in W/m^3; None zeroes it."""
+        """Replace the heat loads with q [nseg, ny, nx] (or [ny, nx] for one
+        segment) in W/m^3; None zeroes them."""
         if q is None:
             _check(self.ctx, load().brahms_heat_set(self.ctx, None))
             return
-        a = np.ascontiguousarray(q, dtype=np.float64).reshape(self.grid.ny, self.grid.nx)
+        a = np.ascontiguousarray(q, dtype=np.float64).reshape(self.nseg, self.grid.ny, self.grid.nx)
         _check(self.ctx, load().brahms_heat_set(self.ctx, a.ctypes.data_as(_dp)))
 
     def thermal_map(self, kappa_th: float, dkdT: float, want_temperature: bool = True):
-        """Solve -kappa_th lap_perp T = Q (T = 0 half a cell outside the window),
-        install dk_map = dkdT * T; returns T [ny, nx] in K (or None)."""
-        t = np.zeros((self.grid.ny, self.grid.nx)) if want_temperature else None
+        """Solve -kappa_th lap_perp T_s = Q_s per z-segment (T = 0 half a cell
+        outside the window) and install dk_map_s = M_s + dkdT * T_s; returns T
+        [ny, nx] in K for one segment, [nseg, ny, nx] for several (or None)."""
+        t = np.zeros((self.nseg, self.grid.ny, self.grid.nx)) if want_temperature else None
         _check(self.ctx, load().brahms_thermal_map(self.ctx, float(kappa_th), float(dkdT),
                                                    None if t is None else t.ctypes.data_as(_dp)))
-        return t
+        return t if t is None or self.nseg > 1 else t[0]
 
     def sync(self):
         _check(self.ctx, load().brahms_sync(self.ctx))

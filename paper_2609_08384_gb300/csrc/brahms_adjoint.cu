@@ -124,6 +124,7 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
   // any failure below leaves no forward for brahms_adjoint_backward to reverse
   ctx->adj_ready = false;
   if (ctx->ny < 2 || ctx->nt < 2) return fail(ctx, BRAHMS_E_SIZE, "the adjoint needs ny >= 2 and nt >= 2");
+  if (ctx->nseg > 1) return fail(ctx, BRAHMS_E_STATE, "the adjoint takes a mismatch map constant in z");
   if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
     return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
   if (phi && (phi_field < 0 || phi_field >= ctx->nf)) return fail(ctx, BRAHMS_E_ARG, "phi_field out of range");

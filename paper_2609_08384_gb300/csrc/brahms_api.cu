@@ -107,14 +107,18 @@ brahms_status brahms_init_grid(brahms_ctx** out, int nx, int ny, int nt, double 
   ctx->energy_dev = (double*)(ctx->ws + ctx->L.energy);
   ctx->dev_err = (int*)(ctx->ws + ctx->L.err);
   ctx->diag_dev = (double*)(ctx->ws + ctx->L.diag);
-  ctx->dkmap_dev = (double*)(ctx->ws + ctx->L.dkmap);
-  ctx->usermap_dev = (double*)(ctx->ws + ctx->L.usermap);
+  ctx->ws_map = (double*)(ctx->ws + ctx->L.dkmap);
+  ctx->ws_umap = (double*)(ctx->ws + ctx->L.usermap);
+  ctx->maps_dev = ctx->ws_map;
+  ctx->umaps_dev = ctx->ws_umap;
+  ctx->mphase_dev = (double*)(ctx->ws + ctx->L.mphase);
   ctx->emap_dev = (float2*)(ctx->ws + ctx->L.emap);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = brahms::upload_twiddles(ctx->twx, nx, ctx->stream);
   if (e == cudaSuccess && ny > 1) e = brahms::upload_twiddles(ctx->twy, ny, ctx->stream);
   if (e == cudaSuccess && nt > 1) e = brahms::upload_twiddles(ctx->twt, nt, ctx->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mphase_dev, 0, sizeof(double) * nx * ny, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e != cudaSuccess) {
     brahms_free(ctx);
@@ -141,6 +145,7 @@ void brahms_free(brahms_ctx* ctx) {
   if (ctx->own_ws && ctx->ws) cudaFree(ctx->ws);
   if (ctx->adj_mem) cudaFree(ctx->adj_mem);
   if (ctx->th_mem) cudaFree(ctx->th_mem);
+  if (ctx->seg_mem) cudaFree(ctx->seg_mem);
   if (ctx->energy_host) cudaFreeHost(ctx->energy_host);
   delete ctx;
 }
@@ -171,6 +176,10 @@ brahms_status brahms_set_fields(brahms_ctx* ctx, const void* const* fields, int 
   ctx->z = 0.0;
   ctx->phi = 0.0;
   ctx->step = 0;
+  {
+    const brahms_status sr = map_phase_reset(ctx);
+    if (sr != BRAHMS_OK) return sr;
+  }
   ctx->have_fields = true;
   touch(ctx);
   brahms_status s = finish_with_check(ctx);
@@ -335,24 +344,67 @@ brahms_status brahms_transform(brahms_ctx* ctx, int direction) {
   return BRAHMS_OK;
 }
 
-brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
+brahms_status brahms_set_dk_map_z(brahms_ctx* ctx, int nseg, const double* z_edges, const double* maps) {
   if (!ctx) return BRAHMS_E_ARG;
-  if (!dk_map) {
-    ctx->have_map = false;
-    ctx->have_user_map = false;
-    touch(ctx);
-    return BRAHMS_OK;
+  if (nseg < 1 || nseg > kMaxMapSegments) return fail(ctx, BRAHMS_E_ARG, "nseg out of range");
+  if (nseg > 1 && !z_edges) return fail(ctx, BRAHMS_E_ARG, "z_edges is NULL");
+  for (int i = 0; i + 1 < nseg; ++i)
+    if (!std::isfinite(z_edges[i]) || !(z_edges[i] > (i ? z_edges[i - 1] : 0.0)))
+      return fail(ctx, BRAHMS_E_ARG, "z_edges must be finite, positive and increasing");
+  const size_t nxy = (size_t)ctx->nx * ctx->ny;
+  if (maps)
+    for (size_t i = 0; i < nxy * nseg; ++i)
+      if (!std::isfinite(maps[i])) return fail(ctx, BRAHMS_E_ARG, "dk_map has non-finite entries");
+  // the maps in effect so far keep their share of the phase
+  brahms_status s = map_phase_sync(ctx);
+  if (s != BRAHMS_OK) return s;
+  if (nseg != ctx->nseg) {
+    BR_CK(cudaStreamSynchronize(ctx->stream));
+    if (ctx->seg_mem) cudaFree(ctx->seg_mem);
+    ctx->seg_mem = nullptr;
+    ctx->maps_dev = ctx->ws_map;
+    ctx->umaps_dev = ctx->ws_umap;
+    ctx->nseg = 1;
+    ctx->zedge.clear();
+    ctx->have_user_map = ctx->have_therm = false;
+    if (nseg > 1) {
+      const size_t plane = align256(sizeof(double) * nxy * nseg);
+      if (brahms::dev_alloc((void**)&ctx->seg_mem, 2 * plane) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->seg_mem = nullptr;
+        update_have_map(ctx);
+        return fail(ctx, BRAHMS_E_OOM, "z-segment maps");
+      }
+      ctx->maps_dev = (double*)ctx->seg_mem;
+      ctx->umaps_dev = (double*)(ctx->seg_mem + plane);
+    }
+    // heat loads belong to the old segments
+    ctx->have_heat.clear();
+  } else if (nseg > 1 && !std::equal(ctx->zedge.begin(), ctx->zedge.end(), z_edges)) {
+    ctx->have_heat.clear();
   }
-  const size_t n = (size_t)ctx->nx * ctx->ny;
-  for (size_t i = 0; i < n; ++i)
-    if (!std::isfinite(dk_map[i])) return fail(ctx, BRAHMS_E_ARG, "dk_map has non-finite entries");
-  BR_CK(cudaMemcpyAsync(ctx->dkmap_dev, dk_map, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
-  BR_CK(cudaMemcpyAsync(ctx->usermap_dev, ctx->dkmap_dev, sizeof(double) * n, cudaMemcpyDeviceToDevice, ctx->stream));
+  ctx->nseg = nseg;
+  if (nseg > 1)
+    ctx->zedge.assign(z_edges, z_edges + (nseg - 1));
+  else
+    ctx->zedge.clear();
+  const size_t bytes = sizeof(double) * nxy * nseg;
+  if (maps) {
+    BR_CK(cudaMemcpyAsync(ctx->umaps_dev, maps, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  } else {
+    BR_CK(cudaMemsetAsync(ctx->umaps_dev, 0, bytes, ctx->stream));
+  }
+  BR_CK(cudaMemcpyAsync(ctx->maps_dev, ctx->umaps_dev, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   BR_CK(cudaStreamSynchronize(ctx->stream));
-  ctx->have_map = true;
-  ctx->have_user_map = true;
+  ctx->have_user_map = maps != nullptr;
+  ctx->have_therm = false;
+  update_have_map(ctx);
   touch(ctx);
   return BRAHMS_OK;
+}
+
+brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map) {
+  return brahms_set_dk_map_z(ctx, 1, nullptr, dk_map);
 }
 
 brahms_status brahms_diagnostics(brahms_ctx* ctx, double* power, double* spectrum) {

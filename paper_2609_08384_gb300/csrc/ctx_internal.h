@@ -2,6 +2,7 @@
 // (brahms_api.cu) and adjoint (brahms_adjoint.cu) entry points.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -20,11 +21,12 @@ constexpr double kHbar = 1.054571817e-34;
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 constexpr int kRedBlocks = 152 * 2;  // energy partials per field (all fields' blocks in one wave)
 constexpr int kKinds = 5;
+constexpr int kMaxMapSegments = 4096;  // z-segments of a mismatch map
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 struct Layout {
-  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, dkmap, usermap, emap, total;
+  size_t state, px, py, pt, twx, twy, twt, partial, energy, err, diag, dkmap, usermap, mphase, emap, total;
 };
 
 inline Layout make_layout(int nx, int ny, int nt, int nf) {
@@ -49,6 +51,7 @@ inline Layout make_layout(int nx, int ny, int nt, int nf) {
   L.diag = take(sizeof(double) * 2 * nt * nf);
   L.dkmap = take(sizeof(double) * nx * ny);
   L.usermap = take(sizeof(double) * nx * ny);
+  L.mphase = take(sizeof(double) * nx * ny);
   L.emap = take(sizeof(float2) * 4 * nx * ny);
   L.total = off;
   return L;
@@ -76,11 +79,25 @@ struct brahms_ctx {
   double *partial = nullptr, *energy_dev = nullptr;
   double* energy_host = nullptr;  // pinned, nf entries + the device error word
   double* diag_dev = nullptr;     // diagnostics: power [nf][nt], spectrum [nf][nt]
-  double* dkmap_dev = nullptr;    // transverse mismatch map [ny][nx] (1/m) in effect
-  double* usermap_dev = nullptr;  // the map of brahms_set_dk_map (the thermal map adds to it)
-  float2* emap_dev = nullptr;     // its stage phase factors for one x-pass [4][ny][nx]
-  bool have_map = false;
+  // Transverse mismatch maps, one per z-segment (nseg segments separated by
+  // the nseg - 1 distances zedge; one segment: the workspace's two planes)
+  int nseg = 1;
+  std::vector<double> zedge;
+  double* maps_dev = nullptr;     // maps in effect [nseg][ny][nx] (1/m)
+  double* umaps_dev = nullptr;    // the caller's maps [nseg][ny][nx] (the thermal map adds to them)
+  double* ws_map = nullptr;       // the workspace's planes for one segment
+  double* ws_umap = nullptr;
+  char* seg_mem = nullptr;        // both arrays when nseg > 1
+  float2* emap_dev = nullptr;     // stage phase factors for one x-pass [4][ny][nx]
+  // the map's share of the coupling phase: P (mphase_dev [ny][nx]) is its
+  // integral up to map_zp, map_cur the segment in effect since (-1: none yet)
+  double* mphase_dev = nullptr;
+  double map_zp = 0.0;
+  int map_cur = -1;
+  bool mphase_live = false;       // P may be non-zero (a map changed during this run)
+  bool have_map = false;          // the x-pass takes the map path
   bool have_user_map = false;
+  bool have_therm = false;        // a thermal map is installed
   int* dev_err = nullptr;          // set by kernels whose bounded waits expired
   unsigned long long tma_wait_ns = 2000000000ULL;  // limit of each TMA tile wait (BRAHMS_OPT_TMA_WAIT_US)
   alignas(64) unsigned char tmap_state[128];  // TMA map of the state for the tau-pass
@@ -129,12 +146,13 @@ struct brahms_ctx {
   std::vector<double> adj_weights, adj_dk, adj_phis;
   // thermal model (allocated on first use)
   char* th_mem = nullptr;
-  double* th_heat = nullptr;   // heat load [ny][nx] W/m^3
-  double* th_temp = nullptr;   // temperature rise [ny][nx] K
+  int th_nseg = 0;             // segments th_mem holds
+  double* th_heat = nullptr;   // heat load per segment [nseg][ny][nx] W/m^3
+  double* th_temp = nullptr;   // temperature rise per segment [nseg][ny][nx] K
   double2* th_twx = nullptr;   // sine-transform tables (nx, ny entries)
   double2* th_twy = nullptr;
   int* th_bad = nullptr;       // non-finite temperature flag
-  bool have_heat = false;
+  std::vector<char> have_heat; // per segment: a load was accumulated or set
 
   long long npoints() const { return (long long)nx * ny * nt; }
 };
@@ -266,16 +284,60 @@ inline brahms::XPassArgs xargs(brahms_ctx* c, int mode, double dz) {
   return a;
 }
 
+// segment that holds distance z (the one that starts at z on an edge)
+inline int seg_of(const brahms_ctx* c, double z) {
+  int s = 0;
+  while (s < c->nseg - 1 && c->zedge[s] <= z) ++s;
+  return s;
+}
+
+inline void update_have_map(brahms_ctx* c) { c->have_map = c->have_user_map || c->have_therm || c->mphase_live; }
+
+// Before the maps are replaced: bring P up to the current distance with the
+// map in effect, so that the phase stays continuous where the new maps take
+// over.
+inline brahms_status map_phase_sync(brahms_ctx* ctx) {
+  if (ctx->have_fields && ctx->have_map && ctx->map_cur >= 0 && ctx->z > ctx->map_zp) {
+    const double len = ctx->z - ctx->map_zp;
+    const double* m = ctx->maps_dev + (size_t)ctx->map_cur * ctx->nx * ctx->ny;
+    BR_CK(launch(ctx, 4, 1, [&] {
+      return brahms::run_map_phase_advance(ctx->mphase_dev, m, len, (long long)ctx->nx * ctx->ny, ctx->stream);
+    }));
+    ctx->mphase_live = true;
+  }
+  ctx->map_zp = ctx->z;
+  ctx->map_cur = -1;
+  return BRAHMS_OK;
+}
+
+// A new run (brahms_set_fields): P = 0 from z = 0.
+inline brahms_status map_phase_reset(brahms_ctx* ctx) {
+  if (ctx->mphase_live)
+    BR_CK(cudaMemsetAsync(ctx->mphase_dev, 0, sizeof(double) * ctx->nx * ctx->ny, ctx->stream));
+  ctx->mphase_live = false;
+  ctx->map_zp = 0.0;
+  ctx->map_cur = -1;
+  update_have_map(ctx);
+  return BRAHMS_OK;
+}
+
 // Stage phase factors of the next x-pass under the mismatch map: B applies
 // the second half of the step that starts at distance zB (mismatch phase
-// phiB, mismatch dkB), A the first half of the step that starts at zA.
+// phiB, mismatch dkB), A the first half of the step that starts at zA.  Each
+// step takes the map of the segment that holds its midpoint.
 inline brahms_status enqueue_map_tables(brahms_ctx* ctx, double phiB, double dkB, double zB, double phiA,
                                         double dkA, double zA, double dz) {
   if (!ctx->have_map) return BRAHMS_OK;
+  const size_t nxy = (size_t)ctx->nx * ctx->ny;
+  const int sA = seg_of(ctx, zA + 0.5 * dz);
+  // no map in effect yet: the map of step A starts here (P holds at zA)
+  const int sB = ctx->map_cur >= 0 ? ctx->map_cur : sA;
   brahms::MapArgs m{};
-  m.dkmap = ctx->dkmap_dev;
+  m.mapB = ctx->maps_dev + sB * nxy;
+  m.mapA = ctx->maps_dev + sA * nxy;
+  m.mphase = ctx->mphase_dev;
   m.emap = ctx->emap_dev;
-  m.nxy = (long long)ctx->nx * ctx->ny;
+  m.nxy = (long long)nxy;
   m.phiB = phiB;
   m.dkB = dkB;
   m.zB = zB;
@@ -283,7 +345,14 @@ inline brahms_status enqueue_map_tables(brahms_ctx* ctx, double phiB, double dkB
   m.dkA = dkA;
   m.zA = zA;
   m.dz = dz;
+  m.zp = ctx->map_zp;
+  m.advance = sA != sB;
   BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_map_tables(m, ctx->stream); }));
+  if (m.advance) {
+    ctx->map_zp = zA;
+    ctx->mphase_live = true;
+  }
+  ctx->map_cur = sA;
   return BRAHMS_OK;
 }
 

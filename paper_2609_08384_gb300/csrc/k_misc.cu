@@ -64,11 +64,18 @@ __device__ __forceinline__ float2 phase_plus(double phi) {
 __global__ void map_tables_kernel(const MapArgs a) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.nxy;
        i += (long long)gridDim.x * blockDim.x) {
-    const double m = a.dkmap[i];
-    a.emap[i] = phase_plus(a.phiB + a.dkB * 0.5 * a.dz + m * (a.zB + 0.5 * a.dz));
-    a.emap[a.nxy + i] = phase_plus((a.dkB + m) * 0.25 * a.dz);
-    a.emap[2 * a.nxy + i] = phase_plus(a.phiA + m * a.zA);
-    a.emap[3 * a.nxy + i] = phase_plus((a.dkA + m) * 0.25 * a.dz);
+    const double mb = a.mapB[i], ma = a.mapA[i];
+    const double p = a.mphase[i];
+    a.emap[i] = phase_plus(a.phiB + a.dkB * 0.5 * a.dz + p + mb * (a.zB - a.zp + 0.5 * a.dz));
+    a.emap[a.nxy + i] = phase_plus((a.dkB + mb) * 0.25 * a.dz);
+    double pa = p, zpa = a.zp;
+    if (a.advance) {
+      pa = p + mb * (a.zA - a.zp);
+      zpa = a.zA;
+      a.mphase[i] = pa;
+    }
+    a.emap[2 * a.nxy + i] = phase_plus(a.phiA + pa + ma * (a.zA - zpa));
+    a.emap[3 * a.nxy + i] = phase_plus((a.dkA + ma) * 0.25 * a.dz);
   }
 }
 
@@ -76,6 +83,18 @@ cudaError_t run_map_tables(const MapArgs& a, cudaStream_t s) {
   long long g = (a.nxy + 255) / 256;
   if (g > 152 * 8) g = 152 * 8;
   map_tables_kernel<<<(unsigned)g, 256, 0, s>>>(a);
+  return cudaPeekAtLastError();
+}
+
+__global__ void map_phase_advance_kernel(double* mphase, const double* m, double len, long long nxy) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nxy; i += (long long)gridDim.x * blockDim.x)
+    mphase[i] += m[i] * len;
+}
+
+cudaError_t run_map_phase_advance(double* mphase, const double* m, double len, long long nxy, cudaStream_t s) {
+  long long g = (nxy + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  map_phase_advance_kernel<<<(unsigned)g, 256, 0, s>>>(mphase, m, len, nxy);
   return cudaPeekAtLastError();
 }
 

@@ -616,13 +616,24 @@ cudaError_t run_prop_tables(const TableArgs& a, cudaStream_t s);
 //   emap[0] = e^{i (phiB + dkB dz/2 + m (zj + dz/2))},  emap[1] = e^{i (dkB + m) dz/4},
 //   emap[2] = e^{i (phiA + m zA)},                        emap[3] = e^{i (dkA + m) dz/4},
 // each [ny][nx]; phases in FP64 reduced mod 2 pi before the FP32 sincos.
+// The map's share of the coupling phase at a point is Q = P + m (z - zp):
+// P the integral of the maps in effect before zp, m the map in effect since.
+// mapB is the map of the step whose B half step this x-pass applies, mapA
+// that of the next step's A half step; when they differ (advance != 0) the
+// kernel brings P up to zA (P += mapB (zA - zp)) and the A factors start
+// from there.
 struct MapArgs {
-  const double* dkmap;
+  const double* mapB;
+  const double* mapA;
+  double* mphase;  // P [ny][nx]
   float2* emap;
   long long nxy;
-  double phiB, dkB, zB, phiA, dkA, zA, dz;
+  double phiB, dkB, zB, phiA, dkA, zA, dz, zp;
+  int advance;
 };
 cudaError_t run_map_tables(const MapArgs& a, cudaStream_t s);
+// P += m * len at every point (a map replaced between propagations)
+cudaError_t run_map_phase_advance(double* mphase, const double* m, double len, long long nxy, cudaStream_t s);
 // the linear step's multiply element by element (grids with nt = 1)
 cudaError_t run_prop_pointwise(const AxisArgs& a, int nf, cudaStream_t s);
 // diagnostics (k_diag.cu): out[f nt + k] = sum_{x,y} |A_f(tau_k)|^2, and

@@ -54,7 +54,8 @@ def test_status_strings_without_gpu(lib):
 CTX_CALLS = ["brahms_set_fields", "brahms_set_dk_profile", "brahms_propagate", "brahms_get_fields", "brahms_energy",
              "brahms_sync", "brahms_transform", "brahms_set_dk_map", "brahms_diagnostics", "brahms_heat_accumulate",
              "brahms_heat_set", "brahms_thermal_map", "brahms_get_z", "brahms_timing", "brahms_set_option",
-             "brahms_adjoint_forward", "brahms_adjoint_backward", "brahms_shg_efficiency_weights"]
+             "brahms_adjoint_forward", "brahms_adjoint_backward", "brahms_shg_efficiency_weights",
+             "brahms_set_dk_map_z", "brahms_heat_accumulate_segment"]
 
 
 def test_null_context_is_an_argument_error_without_gpu(lib):

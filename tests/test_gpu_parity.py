@@ -498,6 +498,88 @@ def test_dk_map_zero_uniform_and_cleared():
     assert rel_l2(grads[0][1], grads[1][1]) < 1e-4
 
 
+def _z_maps(m):
+    # strong enough (up to ~8000 1/m) that the wrong phase rule is far outside the tolerance
+    return 10.0 * np.stack([m, 300.0 - 0.6 * m, 0.4 * m - 500.0])
+
+
+@pytest.mark.parametrize("shape,nf,calls", [((48, 24, 96), 3, (7, 9)), ((48, 24, 96), 3, (4, 8, 4)),
+                                            ((64, 64, 1), 2, (3, 6, 7))],
+                         ids=["48x24x96_f3_split7", "48x24x96_f3_split_at_edge", "64x64x1_f2_three_calls"])
+def test_dk_map_z_matches_oracle(shape, nf, calls):
+    """A map that changes along z (three segments; edges between step
+    midpoints, so steps 0-3, 4-11 and 12-15 take the three maps) with a step
+    profile, over propagate calls that split segments or end on an edge:
+    against the oracle's integral-phase propagation."""
+    br = _br()
+    g, fields, init, m = _map_case(*shape, nf, sum(shape) + nf + 1)
+    maps = _z_maps(m)
+    prof = np.random.default_rng(13).normal(0.0, 300.0, 12)
+    nz, dz, dk = 16, 8 * wl.UM, 700.0
+    edges = [4.3 * dz, 11.6 * dz]
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map_z(edges, maps)
+    s.set_dk_profile(prof)
+    s.set_fields(_dev(init))
+    for n in calls:
+        s.propagate(n, dz)
+    got = s.get_fields()
+    s.close()
+    dks = np.full(nz, dk)
+    dks[:12] = prof
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    ref, _ = oracle.propagate_map_z(prob, [_c64(a).astype(np.complex128) for a in init], nz, dz, dks, edges, maps)
+    errs = [rel_l2(got[f], ref[f]) for f in range(nf)]
+    record("dk_map_z_" + "x".join(map(str, shape)) + f"_f{nf}_" + "_".join(map(str, calls)), field_rel_l2=errs)
+    for f in range(nf):
+        assert errs[f] < FIELD_TOL, (f, errs[f])
+    # a static map (the first segment's) everywhere is clearly another result
+    alt, _ = oracle.propagate_map(prob, [_c64(a).astype(np.complex128) for a in init], nz, dz, dks, maps[0])
+    assert max(rel_l2(alt[f], ref[f]) for f in range(nf)) > 30 * FIELD_TOL
+
+
+def test_map_replaced_between_calls_keeps_the_phase_continuous():
+    """set_dk_map between propagate calls: the new map applies from the current
+    z and the phase stays the integral of the mismatch -- the oracle's
+    z-resolved run with edges at the call boundaries, and the GPU's own
+    z-resolved run, agree with it.  Removing the map mid-run keeps the phase
+    the map accumulated so far."""
+    br = _br()
+    g, fields, init, m = _map_case(32, 16, 32, 3, 41)
+    m = 10.0 * m
+    m2 = 2500.0 - 0.8 * m
+    nz, dz, dk = 14, 8 * wl.UM, 700.0
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map(m)
+    s.set_fields(_dev(init))
+    s.propagate(5, dz)
+    s.set_dk_map(m2)
+    s.propagate(6, dz)
+    s.set_dk_map(None)
+    s.propagate(3, dz)
+    replaced = s.get_fields()
+    edges = [5 * dz, 11 * dz]
+    maps = np.stack([m, m2, np.zeros_like(m)])
+    s.set_dk_map_z(edges, maps)
+    s.set_fields(_dev(init))
+    s.propagate(nz, dz)
+    zres = s.get_fields()
+    s.close()
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    ref, _ = oracle.propagate_map_z(prob, [_c64(a).astype(np.complex128) for a in init], nz, dz, dk, edges, maps)
+    errs = [rel_l2(replaced[f], ref[f]) for f in range(3)]
+    record("dk_map_replaced_between_calls_32x16x32_f3", field_rel_l2=errs)
+    for f in range(3):
+        assert errs[f] < FIELD_TOL, (f, errs[f])
+        assert rel_l2(zres[f], replaced[f]) < 1e-6
+    # the jump the old rule made (map in effect times z from z = 0) is far off
+    prob_jump = [_c64(a).astype(np.complex128) for a in init]
+    a1, ph = oracle.propagate_map(prob, prob_jump, 5, dz, dk, m)
+    a2, ph = oracle.propagate_map(prob, list(a1), 6, dz, dk, m2, phi0=ph, z0=5 * dz)
+    a3, _ = oracle.propagate(prob, list(a2), 3, dz, dk, phi0=ph)
+    assert max(rel_l2(a3[f], ref[f]) for f in range(3)) > 30 * FIELD_TOL
+
+
 EXTREME = [(4096, 2, 2), (2, 4096, 2), (2, 2, 4096), (768, 6, 4), (6, 768, 4), (4, 6, 768), (2, 2, 2)]
 
 

@@ -167,6 +167,97 @@ def test_thermal_map_drives_the_mismatch_map():
     assert np.linalg.norm(plain[0] - want[0]) / np.linalg.norm(want[0]) > 1e-2
 
 
+def test_z_resolved_thermal_map_drives_the_mismatch_map():
+    """Two z-segments with their own heat loads (strong cw SHG whose load grows
+    along z as the absorbing SH builds up): each segment's load sampled at
+    its ends and middle (trapezoid), one temperature per segment, and the
+    propagation under the z-resolved map -- the same chain through the oracle
+    (heat_load, thermal_solve per segment, propagate_map_z)."""
+    br = _br()
+    n_f, n_sh, lam, w0 = wl.N_F, wl.N_SH, wl.LAM_F, 25e-6
+    fields = [wl.FieldParams(lam / 2, n_sh, alpha=60.0), wl.FieldParams(lam, n_f, alpha=5.0)]
+    g = wl.Grid(96, 64, 1, 2.5e-6, 3e-6, 1e-15)
+    x, y, _ = g.axes()
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    a_f = (2e7 * np.exp(-r2 / w0**2))[None].astype(np.complex128)
+    a_sh = np.zeros_like(a_f)
+    L, nz, dk = 4e-3, 80, 0.0
+    dz = L / nz
+    q4 = nz // 4
+    prob = oracle.make_problem(g, fields, wl.D_EFF)
+    kap = 4.6
+    # oracle chain: fields at z = 0, L/4, L/2, 3L/4, L without a map
+    f = [[a_sh, a_f]]
+    ph = 0.0
+    for _ in range(4):
+        nxt, ph = oracle.propagate(prob, list(f[-1]), q4, dz, dk, phi0=ph)
+        f.append(list(nxt))
+    q = [oracle.heat_load(prob, a) for a in f]
+    q_seg = [0.25 * q[0] + 0.5 * q[1] + 0.25 * q[2], 0.25 * q[2] + 0.5 * q[3] + 0.25 * q[4]]
+    t_orc = np.stack([oracle.thermal_solve(qs, g.dx, g.dy, kap) for qs in q_seg])
+    assert t_orc[1].max() > 1.5 * t_orc[0].max()  # the load grows along z
+    dkdT = 6.0 / (t_orc.max() * L)
+    want, _ = oracle.propagate_map_z(prob, f[0], nz, dz, dk, [L / 2], dkdT * t_orc)
+    # GPU chain
+    s = br.Solver(g, fields, wl.D_EFF, dk)
+    s.set_dk_map_z([L / 2])
+    s.set_fields(_dev(f[0]))
+    s.heat_accumulate(0.0, 0.25, segment=0)
+    s.propagate(q4, dz)
+    s.heat_accumulate(0.0, 0.5)                 # z = L/4: the segment that holds z
+    s.propagate(q4, dz)
+    s.heat_accumulate(0.0, 0.25, segment=0)
+    s.heat_accumulate(0.0, 0.25, segment=1)
+    s.propagate(q4, dz)
+    s.heat_accumulate(0.0, 0.5)                 # z = 3L/4
+    s.propagate(q4, dz)
+    s.heat_accumulate(0.0, 0.25, segment=1)
+    t_gpu = s.thermal_map(kap, dkdT)
+    assert t_gpu.shape == (2, g.ny, g.nx)
+    s.set_fields(_dev(f[0]))
+    s.propagate(nz, dz)
+    got = [np.asarray(a) for a in s.get_fields()]
+    s.close()
+    assert np.abs(t_gpu - t_orc).max() / t_orc.max() < 1e-5
+    for k in range(2):
+        err = np.linalg.norm(got[k] - want[k]) / np.linalg.norm(want[k])
+        assert err < 1e-4, (k, err)
+    # the z-averaged map (one segment under the mean load) gives another result
+    avg, _ = oracle.propagate_map(prob, f[0], nz, dz, dk, dkdT * oracle.thermal_solve(0.5 * (q_seg[0] + q_seg[1]),
+                                                                                       g.dx, g.dy, kap))
+    assert np.linalg.norm(avg[0] - want[0]) / np.linalg.norm(want[0]) > 3e-3
+
+
+def test_z_segment_status_codes():
+    br = _br()
+    g = wl.Grid(16, 8, 4, 2e-6, 2e-6, 10e-15)
+    s = br.Solver(g, _fields(2), wl.D_EFF, 0.0)
+    for edges in ([0.0], [2e-3, 1e-3], [float("nan")], [-1e-3]):
+        with pytest.raises(br.BrahmsError) as ei:
+            s.set_dk_map_z(edges)
+        assert ei.value.status == br.BRAHMS_E_ARG
+    s.set_dk_map_z([1e-3, 2e-3])
+    z = np.zeros((4, 8, 16), np.complex64)
+    s.set_fields(_dev([z, z]))
+    with pytest.raises(br.BrahmsError) as ei:
+        s.heat_accumulate(0.0, 1.0, segment=3)
+    assert ei.value.status == br.BRAHMS_E_ARG
+    s.heat_accumulate(0.0, 1.0, segment=0)
+    with pytest.raises(br.BrahmsError) as ei:
+        s.thermal_map(1.0, 1.0)  # segments 1 and 2 have no load
+    assert ei.value.status == br.BRAHMS_E_STATE
+    s.heat_set(np.ones((3, 8, 16)))
+    t = s.thermal_map(1.0, 1.0)
+    assert t.shape == (3, 8, 16) and (t > 0).all()
+    # the adjoint takes a map constant in z
+    with pytest.raises(br.BrahmsError) as ei:
+        s.adjoint_forward(_dev([z, z]), np.zeros(2), 2, 1e-5, np.array([1.0, 0.0]))
+    assert ei.value.status == br.BRAHMS_E_STATE
+    s.set_dk_map(None)  # back to one segment: the adjoint runs
+    s.adjoint_forward(_dev([z, z]), np.zeros(2), 2, 1e-5, np.array([1.0, 0.0]))
+    s.close()
+
+
 def test_thermal_map_adds_to_a_static_map():
     """A fan-out grating map M set by set_dk_map stays under the thermal map:
     the propagation runs with M + dkdT T, as the oracle's under the same sum."""
