@@ -231,9 +231,14 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
  * kernels that may share the GPU.
  * BRAHMS_OPT_TMA_TAU: value 16 or 8 makes the
  * tau-pass of brahms_propagate a persistent kernel that stages tiles of that
- * many x columns through shared memory with double-buffered TMA copies
- * (needs nt in {256, 512} and nx >= 16, else E_SIZE); 0 (the default) keeps
- * the plain tau-pass (and turns the field streams off while set).
+ * many x columns through shared memory with double-buffered TMA copies; 1
+ * makes it a persistent kernel with two CTAs per SM, each prefetching its
+ * next 16-column tile with a TMA copy while it transforms the current one
+ * (its FFT exchanges go through half the shared memory, one real component
+ * at a time).  Both need nt in {256, 512} and nx >= 16, else E_SIZE; both
+ * compute the plain tau-pass's numbers and measured slower on GB300.  0 (the
+ * default) keeps the plain tau-pass (and turns the field streams off while
+ * set).
  * BRAHMS_OPT_TMA_WAIT_US: the limit, in microseconds (0 .. 2000000, default
  * 2000000 = 2 s), of each wait of the TMA tau-pass for a tile's copy; 0
  * gives up at the first check that finds the copy unfinished.  When a
@@ -241,8 +246,9 @@ brahms_status brahms_timing(brahms_ctx* ctx, int enable, double* ms, long long* 
  * 2 s more), leaves its remaining tiles untransformed and returns; the next
  * synchronising call reports E_TIMEOUT and the fields must be set again.
  * (A short limit makes the waits run out on purpose: the way to test that
- * error path without hanging the GPU.)  E_ARG for an unknown option or
- * value.  brahms_get_option returns the current value or -1. */
+ * error path without hanging the GPU.)
+ * E_ARG for an unknown option or value.  brahms_get_option returns the
+ * current value or -1. */
 enum { BRAHMS_OPT_TMA_TAU = 1, BRAHMS_OPT_FIELD_STREAMS = 2, BRAHMS_OPT_TMA_WAIT_US = 3 };
 brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value);
 int brahms_get_option(const brahms_ctx* ctx, int option);

@@ -475,10 +475,12 @@ brahms_status brahms_set_option(brahms_ctx* ctx, int option, int value) {
       ctx->use_tma = 0;
       return BRAHMS_OK;
     }
-    if (value != 8 && value != 16) return fail(ctx, BRAHMS_E_ARG, "TMA tile width must be 8 or 16 columns");
+    if (value != 1 && value != 8 && value != 16)
+      return fail(ctx, BRAHMS_E_ARG, "TMA tau-pass: 1 (prefetching) or a tile width of 8 or 16 columns");
     if (!brahms::tma_tau_supported(ctx->nx, ctx->nt))
       return fail(ctx, BRAHMS_E_SIZE, "TMA tau-pass needs nt in {256, 512} and nx >= 16");
-    BR_CK(brahms::make_tau_tensor_map(ctx->tmap_state, ctx->state, ctx->nx, ctx->ny, ctx->nt, ctx->nf, value));
+    BR_CK(brahms::make_tau_tensor_map(ctx->tmap_state, ctx->state, ctx->nx, ctx->ny, ctx->nt, ctx->nf,
+                                      value == 1 ? 16 : value));
     ctx->use_tma = value;
     return BRAHMS_OK;
   }

@@ -308,6 +308,7 @@ __host__ __device__ constexpr int fft_ns(int p) {
 // ---------------------------------------------------------------- exchange
 // Contiguous pencil (one row of x): one padding slot per 16 entries.
 struct XchRow {
+  static constexpr bool kSplit = false;
   float2* base;
   __device__ __forceinline__ void st(int pos, float2 v) const { base[pos + (pos >> 4)] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return base[pos + (pos >> 4)]; }
@@ -316,10 +317,21 @@ struct XchRow {
 // Strided pencils: TX neighbouring columns, column index fastest.
 template <int TX>
 struct XchCol {
+  static constexpr bool kSplit = false;
   float2* base;
   int tx;
   __device__ __forceinline__ void st(int pos, float2 v) const { base[pos * TX + tx] = v; }
   __device__ __forceinline__ float2 ld(int pos) const { return base[pos * TX + tx]; }
+};
+// The same layout for one real component at a time: the exchange runs in two
+// rounds (real parts, then imaginary parts) through half the shared memory.
+template <int TX>
+struct XchColSplit {
+  static constexpr bool kSplit = true;
+  float* base;
+  int tx;
+  __device__ __forceinline__ void st(int pos, float v) const { base[pos * TX + tx] = v; }
+  __device__ __forceinline__ float ld(int pos) const { return base[pos * TX + tx]; }
 };
 
 // Twiddle tables hold W = (c, s) as hi + lo float pairs, float4 (ch, sh, cl,
@@ -404,21 +416,51 @@ __device__ __forceinline__ void fft_run(float2 (&v)[PL::E], int t, const X& x, c
   if constexpr (P + 1 < NP) {
     constexpr int R2 = fft_radix<PL, INV>(P + 1);
     constexpr int B2 = E / R2;
-    S::sync();  // earlier readers of the exchange buffer are done
+    if constexpr (X::kSplit) {
+      // real parts, then imaginary parts, through the same buffer
+      float re[E];
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      const int j = t + b * T;
-      const int m = j % NS;
-      const int d = (j / NS) * NS * R + m;
+      for (int c = 0; c < 2; ++c) {
+        S::sync();  // earlier readers of the exchange buffer are done
 #pragma unroll
-      for (int r = 0; r < R; ++r) x.st(d + r * NS, v[b * R + r]);
-    }
-    S::sync();
+        for (int b = 0; b < B; ++b) {
+          const int j = t + b * T;
+          const int m = j % NS;
+          const int d = (j / NS) * NS * R + m;
 #pragma unroll
-    for (int b = 0; b < B2; ++b) {
-      const int j = t + b * T;
+          for (int r = 0; r < R; ++r) x.st(d + r * NS, c == 0 ? v[b * R + r].x : v[b * R + r].y);
+        }
+        S::sync();
 #pragma unroll
-      for (int r = 0; r < R2; ++r) v[b * R2 + r] = x.ld(j + r * (N / R2));
+        for (int b = 0; b < B2; ++b) {
+          const int j = t + b * T;
+#pragma unroll
+          for (int r = 0; r < R2; ++r) {
+            const float u = x.ld(j + r * (N / R2));
+            if (c == 0)
+              re[b * R2 + r] = u;
+            else
+              v[b * R2 + r] = make_float2(re[b * R2 + r], u);
+          }
+        }
+      }
+    } else {
+      S::sync();  // earlier readers of the exchange buffer are done
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int j = t + b * T;
+        const int m = j % NS;
+        const int d = (j / NS) * NS * R + m;
+#pragma unroll
+        for (int r = 0; r < R; ++r) x.st(d + r * NS, v[b * R + r]);
+      }
+      S::sync();
+#pragma unroll
+      for (int b = 0; b < B2; ++b) {
+        const int j = t + b * T;
+#pragma unroll
+        for (int r = 0; r < R2; ++r) v[b * R2 + r] = x.ld(j + r * (N / R2));
+      }
     }
     fft_run<PL, INV, P + 1, X, S, TW>(v, t, x, tw);
   }

@@ -192,6 +192,125 @@ __global__ void __launch_bounds__(PL::T * TX, PL::T * TX <= 256 ? 2 : 1)
   }
 }
 
+// ----------------------------------------------- prefetching tau-pass
+// Persistent CTAs, two per SM, each with one 64 KB prefetch buffer: a tile
+// is copied from the buffer into registers, the CTA synchronises, thread 0
+// starts the copy of the CTA's next tile into the same buffer, and the tile
+// is transformed, multiplied, transformed back and stored while that copy is
+// in flight.  The FFT exchanges go through a separate half-size buffer, one
+// real component at a time, so that two CTAs' buffers fit in an SM; the
+// twiddles are read through L1.  Tiles are taken from the last down (as the
+// plain tau-pass).  Waits are bounded as in the double-buffered kernel.
+template <class PL>
+__host__ __device__ constexpr size_t pre_smem_bytes() {
+  return (size_t)PL::N * 16 * 8 + (size_t)PL::N * 16 * 4 + 16;
+}
+
+template <class PL>
+__global__ void __launch_bounds__(PL::T * 16, 2)
+    tpass_pre_kernel(const __grid_constant__ CUtensorMap tm, const AxisArgs p, int* err, unsigned long long wait_ns) {
+  constexpr int TX = 16;
+  constexpr int N = PL::N, E = PL::E, T = PL::T;
+  constexpr int BOX = tma_box_t<PL>();
+  constexpr int NBOX = N / BOX;
+  constexpr uint32_t TILE_BYTES = (uint32_t)(N * TX * 8);
+  constexpr int R0 = fft_radix<PL, false>(0), RL = fft_radix<PL, false>(PL::NP - 1);
+  constexpr int S0 = N / R0, SL = N / RL;
+  extern __shared__ __align__(1024) unsigned char smraw[];
+  float2* pre = reinterpret_cast<float2*>(smraw);
+  float* xre = reinterpret_cast<float*>(pre + N * TX);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(xre + N * TX);
+  if (smem_u32(smraw) & 127u) {
+    if (threadIdx.x == 0) atomicExch(err, 2);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  const long long ntiles = p.ntiles;
+  auto issue = [&](long long tl) {
+    const int xt = (int)(tl % p.xtiles);
+    const long long rest = tl / p.xtiles;
+    const int y = (int)(rest % p.ny), f = (int)(rest / p.ny);
+    const uint32_t b = smem_u32(bar);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(TILE_BYTES) : "memory");
+#pragma unroll
+    for (int q = 0; q < NBOX; ++q) {
+      const uint32_t dst = smem_u32(pre + (size_t)q * BOX * TX);
+      asm volatile(
+          "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+          "[%6];" ::"r"(dst),
+          "l"(reinterpret_cast<uint64_t>(&tm)), "r"(2 * TX * xt), "r"(y), "r"(q * BOX), "r"(f), "r"(b)
+          : "memory");
+    }
+  };
+
+  const int tx = threadIdx.x % TX, t = threadIdx.x / TX;
+  const TwGlobal tw{p.tw};
+  const XchColSplit<TX> xc{xre, tx};
+  uint32_t phase = 0u;
+  long long k = blockIdx.x;  // tile ntiles-1-k
+  if (threadIdx.x == 0 && k < ntiles) issue(ntiles - 1 - k);
+  for (; k < ntiles; k += gridDim.x) {
+    const long long tile = ntiles - 1 - k;
+    const bool ok = mbar_wait(smem_u32(bar), phase, wait_ns);
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+        mbar_wait(smem_u32(bar), phase, kTmaDrainNs);  // the copy in flight lands before the CTA leaves
+      }
+      return;
+    }
+    phase ^= 1u;
+    float2 v[E];
+#pragma unroll
+    for (int bb = 0; bb < E / R0; ++bb)
+#pragma unroll
+      for (int r = 0; r < R0; ++r) v[bb * R0 + r] = pre[(t + bb * T + r * S0) * TX + tx];
+    __syncthreads();  // the buffer is free: fetch the next tile while this one is transformed
+    if (threadIdx.x == 0 && k + gridDim.x < ntiles) issue(ntiles - 1 - (k + gridDim.x));
+    const int xt = (int)(tile % p.xtiles);
+    const long long rest = tile / p.xtiles;
+    const int y = (int)(rest % p.ny), f = (int)(rest / p.ny);
+    const int x = xt * TX + tx;
+    const bool act = x < p.nx;
+    fft_run<PL, false, 0, XchColSplit<TX>, SyncBlock, TwGlobal>(v, t, xc, tw);
+    float2 dxy = make_float2(0.f, 0.f);
+    if (act) {
+      const float2 dx = p.px[f * p.nx + x], dy = p.py[f * p.ny + y];
+      dxy = cadd(cadd(dx, dy), cmul(dx, dy));
+    }
+    if (p.conj_p) dxy.y = -dxy.y;
+    const float2* pt = p.pt + f * p.nt;
+    const float tsign = p.conj_p ? -1.f : 1.f;
+#pragma unroll
+    for (int bb = 0; bb < E / RL; ++bb)
+#pragma unroll
+      for (int r = 0; r < RL; ++r) {
+        const int kk = t + bb * T + r * SL;
+        float2 dt = pt[kk];
+        dt.y *= tsign;
+        float2 w = v[bb * RL + r];
+        w = make_float2(fmaf(w.x, p.scale, w.x * p.scale_lo), fmaf(w.y, p.scale, w.y * p.scale_lo));
+        v[bb * RL + r] = mul_one_plus(w, cadd(cadd(dxy, dt), cmul(dxy, dt)));
+      }
+    fft_run<PL, true, 0, XchColSplit<TX>, SyncBlock, TwGlobal>(v, t, xc, tw);
+    if (act) {
+      float2* base = p.data + (long long)f * p.fstride + (long long)y * p.nx + x;
+      const long long stride = (long long)p.nx * p.ny;
+#pragma unroll
+      for (int bb = 0; bb < E / R0; ++bb)
+#pragma unroll
+        for (int r = 0; r < R0; ++r) base[(t + bb * T + r * S0) * stride] = v[bb * R0 + r];
+    }
+  }
+  // a CTA whose last wait succeeded has no copy in flight here
+}
+
 // ------------------------------------------------------------------- host
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -259,8 +378,40 @@ static cudaError_t launch_tma(const void* map128, const AxisArgs& a0, int* err, 
   return cudaPeekAtLastError();
 }
 
+template <class PL>
+static cudaError_t launch_pre(const void* map128, const AxisArgs& a0, int* err, unsigned long long wait_ns,
+                              cudaStream_t s) {
+  AxisArgs a = a0;  // tiles of 16 columns
+  a.xtiles = (a.nx + 15) / 16;
+  a.ntiles = a0.ntiles / a0.xtiles * a.xtiles;
+  constexpr size_t smem = pre_smem_bytes<PL>();
+  static SmemOnce once;
+  cudaError_t e = raise_smem_limit(tpass_pre_kernel<PL>, smem, once);
+  if (e != cudaSuccess) return e;
+  int dev = 0, per_sm = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tpass_pre_kernel<PL>, PL::T * 16, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  long long grid = (long long)sms * per_sm;
+  if (grid > a.ntiles) grid = a.ntiles;
+  if (grid <= 0) return cudaSuccess;
+  CUtensorMap m;
+  memcpy(&m, map128, sizeof(m));
+  tpass_pre_kernel<PL><<<(unsigned)grid, PL::T * 16, smem, s>>>(m, a, err, wait_ns);
+  return cudaPeekAtLastError();
+}
+
 cudaError_t run_tpass_prop_tma(int nt, int tx, const void* map128, const AxisArgs& a, int* err,
                                unsigned long long wait_ns, cudaStream_t s) {
+  if (tx == 1) {  // prefetching form (16-column tiles)
+    switch (nt) {
+      case 256: return launch_pre<TauPlan<256>>(map128, a, err, wait_ns, s);
+      case 512: return launch_pre<TauPlan<512>>(map128, a, err, wait_ns, s);
+      default: return cudaErrorNotSupported;
+    }
+  }
   if (tx == 8) {
     switch (nt) {
       case 256: return launch_tma<TauPlan<256>, 8>(map128, a, err, wait_ns, s);

@@ -43,7 +43,8 @@ def _opg_small():
     return g, fields, [torch.from_numpy(a.astype(np.complex64)).cuda() for a in init]
 
 
-def test_tma_tau_wait_limit_runs_out_and_the_context_recovers():
+@pytest.mark.parametrize("form", [16, 1], ids=["double_buffered", "prefetching"])
+def test_tma_tau_wait_limit_runs_out_and_the_context_recovers(form):
     """TMA tau-pass with a zero wait limit: the waits for the tiles' copies run
     out, the kernel lets its copies land and returns, the next synchronising
     call reports E_TIMEOUT; with the default limit and the fields set again
@@ -56,7 +57,7 @@ def test_tma_tau_wait_limit_runs_out_and_the_context_recovers():
     ref.propagate(6, 10 * wl.UM)
     want = ref.get_fields()
     ref.close()
-    s.set_option(br.BRAHMS_OPT_TMA_TAU, 16)
+    s.set_option(br.BRAHMS_OPT_TMA_TAU, form)
     assert s.get_option(br.BRAHMS_OPT_TMA_WAIT_US) == 2000000
     s.set_option(br.BRAHMS_OPT_TMA_WAIT_US, 0)
     s.set_fields(dev)
