@@ -422,11 +422,12 @@ def thermal_form(solver, problem, dev, reps=5):
     return out
 
 
-def adjoint_form(dev):
+def adjoint_form(dev, store_all=True):
     """SHG efficiency gradient on 128x128x256 over 400 steps (256-entry spectral
     phase, 400-entry mismatch profile), sqrt(nz) checkpointing: the time of the
     checkpointed forward plus the reverse sweep, against the plain forward of
-    the same propagation.  CUDA events on the solver stream."""
+    the same propagation.  CUDA events on the solver stream.  store_all also
+    times the form that records every step (54 GB of states)."""
     import torch
 
     import paper_2609_08384_gb300 as br
@@ -458,6 +459,19 @@ def adjoint_form(dev):
     e0.record(stream)
     torch.cuda.synchronize(dev)
     ms_fwd, ms_bwd, ms_plain = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), e[3].elapsed_time(e0)
+    units = float(p.grid.npoints * 2 * p.nz)
+    out = {"value": units / ((ms_fwd + ms_bwd) / 1e3), "unit": UNIT, "eta": J,
+           "ms_forward_checkpointed": ms_fwd, "ms_backward": ms_bwd, "ms_plain_forward": ms_plain,
+           "gradient_cost_vs_plain_forward": (ms_fwd + ms_bwd) / ms_plain,
+           # bytes moved by design per grid point, field and step (the per-segment
+           # checkpoint copies left out): forward 4 passes (64 B); backward the
+           # recording recomputation (64 B + 2 writes of 8 B) and the reverse
+           # passes (64 B + 2 reads of 8 B)
+           "moved_GB_per_s_design": 224.0 * units / ((ms_fwd + ms_bwd) / 1e3) / 1e9,
+           "workload": "SHG 128x128x256, 400 steps of 5 um, d eta / d(phi[256], dk[400])"}
+    if not store_all:
+        s.close()
+        return out
     # every step recorded in the forward (2 nz states, 54 GB here): no recomputation in the backward
     s.adjoint_forward(dev_in, p.dk_profile, p.nz, p.dz, w, phi=p.spectral_phase, checkpoint_interval=-1)
     s.adjoint_backward(1.0)
@@ -470,22 +484,13 @@ def adjoint_form(dev):
     torch.cuda.synchronize(dev)
     ms_fwd_all, ms_bwd_all = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
     s.close()
-    units = float(p.grid.npoints * 2 * p.nz)
-    return {"value": units / ((ms_fwd + ms_bwd) / 1e3), "unit": UNIT, "eta": J,
-            "ms_forward_checkpointed": ms_fwd, "ms_backward": ms_bwd, "ms_plain_forward": ms_plain,
-            "gradient_cost_vs_plain_forward": (ms_fwd + ms_bwd) / ms_plain,
-            # bytes moved by design per grid point, field and step (the per-segment
-            # checkpoint copies left out): forward 4 passes (64 B); backward the
-            # recording recomputation (64 B + 2 writes of 8 B) and the reverse
-            # passes (64 B + 2 reads of 8 B)
-            "moved_GB_per_s_design": 224.0 * units / ((ms_fwd + ms_bwd) / 1e3) / 1e9,
-            "store_all": {"value": units / ((ms_fwd_all + ms_bwd_all) / 1e3), "ms_forward_recording": ms_fwd_all,
-                          "ms_backward": ms_bwd_all,
-                          "gradient_cost_vs_plain_forward": (ms_fwd_all + ms_bwd_all) / ms_plain,
-                          # recording forward (80 B) and reverse passes (80 B)
-                          "moved_GB_per_s_design": 160.0 * units / ((ms_fwd_all + ms_bwd_all) / 1e3) / 1e9,
-                          "state_memory_GB": 2 * p.nz * p.grid.npoints * 2 * 8 / 1e9},
-            "workload": "SHG 128x128x256, 400 steps of 5 um, d eta / d(phi[256], dk[400])"}
+    out["store_all"] = {"value": units / ((ms_fwd_all + ms_bwd_all) / 1e3), "ms_forward_recording": ms_fwd_all,
+                        "ms_backward": ms_bwd_all,
+                        "gradient_cost_vs_plain_forward": (ms_fwd_all + ms_bwd_all) / ms_plain,
+                        # recording forward (80 B) and reverse passes (80 B)
+                        "moved_GB_per_s_design": 160.0 * units / ((ms_fwd_all + ms_bwd_all) / 1e3) / 1e9,
+                        "state_memory_GB": 2 * p.nz * p.grid.npoints * 2 * 8 / 1e9}
+    return out
 
 
 def e2e_pipelined(solvers, host_in, host_out, problem, steps):
@@ -727,6 +732,8 @@ def run_ours(args):
         forms["batched_small_grids"] = batched_form(dev, small=True)
     if want("adjoint"):
         forms["adjoint"] = adjoint_form(dev)
+    elif want("adjoint_checkpointed"):
+        forms["adjoint"] = adjoint_form(dev, store_all=False)
 
     if rank != 0:
         return 0
@@ -761,7 +768,8 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and adjoint forms")
     ap.add_argument("--forms", default=None,
                     help="comma-separated subset of the forms (diagnostics, thermal, cw_focused_shg, dk_map, "
-                         "batched, batched_small_grids, adjoint); default all")
+                         "batched, batched_small_grids, adjoint, adjoint_checkpointed); default all but "
+                         "adjoint_checkpointed (adjoint includes it)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
