@@ -32,7 +32,7 @@ brahms_status thermal_alloc(brahms_ctx* ctx) {
       return o;
     };
     const size_t o_h = take(sizeof(double) * nxy * ctx->nseg), o_t = take(sizeof(double) * nxy * ctx->nseg);
-    const size_t o_x = take(sizeof(double2) * ctx->nx), o_y = take(sizeof(double2) * ctx->ny);
+    const size_t o_x = take(sizeof(double2) * 2 * ctx->nx), o_y = take(sizeof(double2) * 2 * ctx->ny);
     const size_t o_b = take(sizeof(int));
     if (brahms::dev_alloc((void**)&ctx->th_mem, off) != cudaSuccess) {
       cudaGetLastError();

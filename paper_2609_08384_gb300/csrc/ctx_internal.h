@@ -149,7 +149,7 @@ struct brahms_ctx {
   int th_nseg = 0;             // segments th_mem holds
   double* th_heat = nullptr;   // heat load per segment [nseg][ny][nx] W/m^3
   double* th_temp = nullptr;   // temperature rise per segment [nseg][ny][nx] K
-  double2* th_twx = nullptr;   // sine-transform tables (nx, ny entries)
+  double2* th_twx = nullptr;   // sine-transform tables (2 nx, 2 ny entries)
   double2* th_twy = nullptr;
   int* th_bad = nullptr;       // non-finite temperature flag
   std::vector<char> have_heat; // per segment: a load was accumulated or set

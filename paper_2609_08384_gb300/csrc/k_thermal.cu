@@ -10,11 +10,16 @@
 //                    k = 1..n, are the eigenvectors of the 3-point second
 //                    difference, with eigenvalues -4 sin^2(pi k / (2n)) / d^2;
 //                    analysis along x and y, a division by the eigenvalues
-//                    and synthesis solve the 5-point system exactly.  Each
-//                    analysis or synthesis of a line is one complex FFT of
-//                    length 2n (odd extension) in FP64 shared memory: an
-//                    in-place Stockham FFT, radix 2 and 3, with one barrier
-//                    between the reads and the writes of every stage.
+//                    and synthesis solve the 5-point system exactly.  A line's
+//                    analysis is a real-input sine transform computed through
+//                    one complex FFT of n/2 points (Makhoul's packing of a
+//                    real sequence for the cosine transform, IEEE Trans. ASSP
+//                    28 (1980), with the sine transform read off the cosine
+//                    transform of the sign-alternated line), and its
+//                    synthesis undoes those steps one by one.  The FFT is an
+//                    in-place Stockham FFT in FP64 shared memory, radix 2 and
+//                    3, with one barrier between the reads and the writes of
+//                    every stage.
 #include "kernels.cuh"
 #include "launch_cfg.h"
 
@@ -25,17 +30,17 @@ namespace {
 constexpr int kHeatX = 64;    // x-points per CTA (32 pairs)
 constexpr int kHeatLanes = 8;  // tau-lanes per CTA
 constexpr int kHeatU = 8;      // tau samples per thread and iteration
-constexpr int kSineThreads = 512;
-constexpr int kSineMaxB2 = 8;  // radix-2 butterflies per thread: m / 2 <= 8 * 512, m <= 8192
-constexpr int kSineMaxB3 = 2;  // radix-3 butterflies per thread: m / 3 <= 2 * 512
+constexpr int kSineThreads = 256;
+constexpr int kSineMaxB2 = 8;  // radix-2 butterflies per thread: m / 2 <= 8 * 256, m <= 4096
+constexpr int kSineMaxB3 = 2;  // radix-3 butterflies per thread: m / 3 <= 2 * 256
 constexpr int kSineMaxStages = 16;
 
 struct SineArgs {
   double* d;
-  const double2* tw;  // n entries: e^{-2 pi i j / m}, j < m / 2, m = 2n
+  const double2* tw;  // 2n entries: e^{-i pi j / n} (j < n), then e^{-i pi k / (2n)} (k < n)
   long long elem;     // stride between the entries of a line
   long long pitch;    // stride between lines
-  int n;
+  int n;              // line length (even); the FFT has m = n / 2 points
   int nst;
   int rad[kSineMaxStages];
 };
@@ -44,10 +49,11 @@ __device__ __forceinline__ double2 z_mul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// e^{-+2 pi i e / m}, 0 <= e < m, from the half table
+// e^{-+2 pi i e / m}, 0 <= e < m, m = n / 2, from the table of e^{-i pi j / n}
+// (the entry 4 e for e < m / 2, and its negative above)
 __device__ __forceinline__ double2 sine_tw(const double2* tw, int m, int e, bool inv) {
   const int h = m >> 1;
-  double2 w = e < h ? tw[e] : make_double2(-tw[e - h].x, -tw[e - h].y);
+  double2 w = e < h ? tw[4 * e] : make_double2(-tw[4 * (e - h)].x, -tw[4 * (e - h)].y);
   if (inv) w.y = -w.y;
   return w;
 }
@@ -120,51 +126,94 @@ __device__ void fft64_inplace(double2* buf, const SineArgs& a, int m, bool inv) 
 // SYNTH false: S_k = sum_j x_j sin(pi k (j + 1/2) / n), k = 1..n, stored at k - 1.
 // SYNTH true:  x_j = sum_k (a_k / nu_k) sin(pi k (j + 1/2) / n), a_k read at k - 1,
 //              nu_k = n / 2 (k < n) or n (k = n): the inverse of the analysis.
+//
+// Analysis.  With x'_j = (-1)^j x_j, S_k = C_{n-k} (k < n) and S_n = C_0, C the
+// cosine transform C_k = sum_j x'_j cos(pi k (2j + 1) / (2n)).  Packing
+// v_j = x'_{2j}, v_{n-1-j} = x'_{2j+1} (j < n/2) gives C_k = Re(w_k V_k), V the
+// n-point DFT of v and w_k = e^{-i pi k / (2n)}; V of the real v comes from the
+// n/2-point DFT Z of z_q = v_{2q} + i v_{2q+1}:
+//   V_k = E_k + e^{-2 pi i k / n} O_k,  E_k = (Z_k + conj Z_{m-k}) / 2,
+//   O_k = (Z_k - conj Z_{m-k}) / (2i),  k = 0..m (indices of Z mod m),
+// and with V_{n-k} = conj V_k, C_{n-k} = -Im(w_k V_k).
+// Synthesis runs the steps backwards: V_k = conj(w_k) (C_k - i C_{n-k}),
+// Z_q = E_q + i O_q with E_q = (V_q + conj V_{m-q}) / 2 and
+// O_q = e^{2 pi i q / n} (V_q - conj V_{m-q}) / 2, the inverse n/2-point DFT, and
+// the unpacking.
 template <bool SYNTH>
 __global__ void __launch_bounds__(kSineThreads) sine_lines_kernel(const SineArgs a) {
   extern __shared__ double2 zbuf[];
-  const int n = a.n, m = 2 * n;
+  const int n = a.n, m = n / 2;
+  const double2* th = a.tw + n;  // e^{-i pi k / (2n)}
   double* p = a.d + (long long)blockIdx.x * a.pitch;
   if (!SYNTH) {
-    // odd extension: y_j = x_j, y_{m-1-j} = -x_j
-    for (int j = threadIdx.x; j < n; j += kSineThreads) {
-      const double v = p[j * a.elem];
-      zbuf[j] = make_double2(v, 0.0);
-      zbuf[m - 1 - j] = make_double2(-v, 0.0);
+    // z_q = v_{2q} + i v_{2q+1}, v_i = x'_{2i} (i < m) or x'_{2n-1-2i} (i >= m)
+    for (int q = threadIdx.x; q < m; q += kSineThreads) {
+      double c[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = 2 * q + h;
+        const int jj = i < m ? 2 * i : 2 * n - 1 - 2 * i;
+        const double x = p[(long long)jj * a.elem];
+        c[h] = (jj & 1) ? -x : x;
+      }
+      zbuf[q] = make_double2(c[0], c[1]);
     }
   } else {
-    // c_k = (a_k / nu_k) e^{i pi k / (2n)} for k = 1..n, zero elsewhere
-    for (int k = threadIdx.x; k < m; k += kSineThreads) {
-      double2 c = make_double2(0.0, 0.0);
-      if (k >= 1 && k <= n) {
-        const double b = p[(k - 1) * a.elem] / (k < n ? 0.5 * n : (double)n);
-        double sn, cs;
-        sincospi((double)k / (double)m, &sn, &cs);
-        c = make_double2(b * cs, b * sn);
+    // Z_q from the coefficients: C_k = a[n-1-k] (k >= 1), C_0 = a[n-1]
+    for (int q = threadIdx.x; q < m; q += kSineThreads) {
+      double2 v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = h == 0 ? q : m - q;
+        const double ck = k == 0 ? p[(long long)(n - 1) * a.elem] : p[(long long)(n - 1 - k) * a.elem];
+        const double cn = k == 0 ? 0.0 : p[(long long)(k - 1) * a.elem];
+        const double2 w = th[k];  // V_k = conj(w_k) (C_k - i C_{n-k})
+        v[h] = make_double2(w.x * ck - w.y * cn, -w.y * ck - w.x * cn);
       }
-      zbuf[k] = c;
+      const double2 vq = v[0], vc = make_double2(v[1].x, -v[1].y);  // V_q, conj V_{m-q}
+      const double2 e = make_double2(0.5 * (vq.x + vc.x), 0.5 * (vq.y + vc.y));
+      const double2 d = make_double2(0.5 * (vq.x - vc.x), 0.5 * (vq.y - vc.y));
+      const double2 wq = a.tw[2 * q];  // e^{-2 pi i q / n}; O_q = conj(wq) d
+      const double2 o = make_double2(wq.x * d.x + wq.y * d.y, wq.x * d.y - wq.y * d.x);
+      zbuf[q] = make_double2(e.x - o.y, e.y + o.x);  // E + i O
     }
   }
   __syncthreads();
   fft64_inplace(zbuf, a, m, SYNTH);
   if (!SYNTH) {
-    // Y_k e^{-i pi k / (2n)} = -2i S_k
-    for (int k = 1 + threadIdx.x; k <= n; k += kSineThreads) {
-      double sn, cs;
-      sincospi((double)k / (double)m, &sn, &cs);
-      const double2 y = zbuf[k];
-      p[(k - 1) * a.elem] = 0.5 * (sn * y.x - cs * y.y);
+    for (int k = threadIdx.x; k <= m; k += kSineThreads) {
+      const double2 zk = zbuf[k % m], zr = zbuf[(m - k) % m];
+      const double2 zc = make_double2(zr.x, -zr.y);
+      const double2 e = make_double2(0.5 * (zk.x + zc.x), 0.5 * (zk.y + zc.y));
+      const double2 o = make_double2(0.5 * (zk.y - zc.y), -0.5 * (zk.x - zc.x));  // (Z_k - conj Z_{m-k}) / (2i)
+      const double2 wk = k < m ? a.tw[2 * k] : make_double2(-1.0, 0.0);        // e^{-2 pi i k / n}
+      const double2 vk = make_double2(e.x + wk.x * o.x - wk.y * o.y, e.y + wk.x * o.y + wk.y * o.x);
+      const double2 w = th[k];
+      const double ur = w.x * vk.x - w.y * vk.y, ui = w.x * vk.y + w.y * vk.x;  // w_k V_k
+      if (k < m) p[(long long)(k == 0 ? n - 1 : n - 1 - k) * a.elem] = ur;        // C_k
+      if (k >= 1) p[(long long)(k - 1) * a.elem] = -ui;                           // C_{n-k}
     }
   } else {
-    for (int j = threadIdx.x; j < n; j += kSineThreads) p[j * a.elem] = zbuf[j].y;
+    const double inv_m = 1.0 / (double)m;
+    for (int j = threadIdx.x; j < n; j += kSineThreads) {
+      // x_j = (-1)^j x'_j, x'_{2i} = v_i, x'_{2i+1} = v_{n-1-i}, v_i from z_{i/2}
+      const int i = (j & 1) ? n - 1 - (j >> 1) : (j >> 1);
+      const double2 zq = zbuf[i >> 1];
+      const double v = ((i & 1) ? zq.y : zq.x) * inv_m;
+      p[(long long)j * a.elem] = (j & 1) ? -v : v;
+    }
   }
 }
 
+// tw[j] = e^{-i pi j / n} and tw[n + j] = e^{-i pi j / (2n)}, j < n
 __global__ void sine_twiddles_kernel(double2* tw, int n) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= n) return;
+  if (j >= 2 * n) return;
   double sn, cs;
-  sincospi(-(double)j / (double)n, &sn, &cs);  // e^{-2 pi i j / (2n)}
+  if (j < n)
+    sincospi(-(double)j / (double)n, &sn, &cs);
+  else
+    sincospi(-(double)(j - n) / (2.0 * n), &sn, &cs);
   tw[j] = make_double2(cs, sn);
 }
 
@@ -252,7 +301,8 @@ __global__ void __launch_bounds__(kHeatX / 2 * kHeatLanes) heat_load_kernel(cons
 }
 
 bool sine_plan(int n, SineArgs& a) {
-  int m = 2 * n, st = 0;
+  if (n < 2 || n % 2) return false;
+  int m = n / 2, st = 0;
   while (m % 2 == 0) {
     if (st == kSineMaxStages) return false;
     a.rad[st++] = 2;
@@ -266,7 +316,7 @@ bool sine_plan(int n, SineArgs& a) {
   if (m != 1) return false;
   a.nst = st;
   a.n = n;
-  const int mm = 2 * n;
+  const int mm = n / 2;
   for (int s = 0; s < st; ++s) {
     const int nb = mm / a.rad[s];
     const int cap = (a.rad[s] == 2 ? kSineMaxB2 : kSineMaxB3) * kSineThreads;
@@ -284,7 +334,7 @@ cudaError_t sine_lines(double* d, const double2* tw, int n, long long elem, long
   a.tw = tw;
   a.elem = elem;
   a.pitch = pitch;
-  const size_t smem = sizeof(double2) * 2 * (size_t)n;
+  const size_t smem = sizeof(double2) * (size_t)(n / 2);
   static SmemMax limit;
   cudaError_t e = raise_smem_limit_to(sine_lines_kernel<SYNTH>, std::max<size_t>(smem, 48 * 1024), limit);
   if (e != cudaSuccess) return e;
@@ -297,11 +347,11 @@ cudaError_t sine_lines(double* d, const double2* tw, int n, long long elem, long
 bool sine_length_supported(int n) {
   if (n < 2) return false;
   SineArgs a{};
-  return sine_plan(n, a) && sizeof(double2) * 2 * (size_t)n <= 227 * 1024;
+  return sine_plan(n, a) && sizeof(double2) * (size_t)(n / 2) <= 227 * 1024;
 }
 
 cudaError_t run_sine_twiddles(double2* tw, int n, cudaStream_t s) {
-  sine_twiddles_kernel<<<(n + 255) / 256, 256, 0, s>>>(tw, n);
+  sine_twiddles_kernel<<<(2 * n + 255) / 256, 256, 0, s>>>(tw, n);
   return cudaPeekAtLastError();
 }
 

@@ -652,7 +652,7 @@ struct HeatArgs {
   double* heat;  // [ny][nx], accumulated into
 };
 cudaError_t run_heat_load(const HeatArgs& a, cudaStream_t s);
-// sine-transform tables for one axis of length n > 1: n entries
+// sine-transform tables for one axis of even length n > 1: 2n entries
 cudaError_t run_sine_twiddles(double2* tw, int n, cudaStream_t s);
 bool sine_length_supported(int n);
 struct ThermalArgs {
