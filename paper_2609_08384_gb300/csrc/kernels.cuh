@@ -504,7 +504,8 @@ __device__ __forceinline__ void tprop_tile(const AxisArgs& p, long long cta_tile
   // staging issued after this tile's loads instead of before them, 520 us;
   // a persistent loop over tiles, 542 us; the first pass's loads issued in
   // the order the radix-32 codelet consumes them, 549 us; launch bounds of
-  // two CTAs per SM (128 registers), 531 us.)
+  // two CTAs per SM (128 registers), 531 us; the field's tau factors staged
+  // in shared memory with the twiddles, 506 us.)
   float2 dxy = make_float2(0.f, 0.f);
   if (a.act) {
     const float2 dx = p.px[a.f * p.nx + a.x], dy = p.py[a.f * p.ny + a.other];
