@@ -26,6 +26,10 @@ Parity status of each function (what pins it, see tests/test_oracle_*.py):
                       sensitivities and full gradients against central
                       finite differences of objective(), with and without
                       a transverse mismatch map
+  adjoint_gradient    (also under a map that changes along z: uniform
+                      segments give the step-profile gradient, one segment
+                      the static-map gradient, central differences of
+                      objective() with three segments)
   propagate_map_z     piecewise-constant mismatch per column against the
                       undepleted closed form sum_s e^{-i Phi(z_s)} (1 -
                       e^{-i dk_s l_s}) / (i dk_s); uniform segments equal the
@@ -124,6 +128,12 @@ def _load():
             lib.orc_objective.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, dp,
                                           dp]
             lib.orc_objective.restype = ctypes.c_double
+            lib.orc_adjoint_gradient_z.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp,
+                                                   ctypes.c_int, dp, dp, dp, ctypes.c_int, dp, dp]
+            lib.orc_adjoint_gradient_z.restype = ctypes.c_double
+            lib.orc_objective_z.argtypes = [P(_Problem), vp, ctypes.c_int, ctypes.c_double, dp, dp, ctypes.c_int, dp,
+                                            ctypes.c_int, dp, dp]
+            lib.orc_objective_z.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -372,27 +382,48 @@ def _map(prob, dk_map):
     return None if dk_map is None else np.ascontiguousarray(dk_map, dtype=np.float64).reshape(prob.ny, prob.nx)
 
 
-def objective(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None):
+def _zmaps(prob, z_edges, maps):
+    m = np.ascontiguousarray(maps, dtype=np.float64).reshape(-1, prob.ny, prob.nx)
+    e = np.ascontiguousarray(np.asarray(z_edges, dtype=np.float64).reshape(-1))
+    if len(e) != len(m) - 1 or np.any(np.diff(e) <= 0):
+        raise ValueError("need len(maps) - 1 increasing z_edges")
+    return m, (e if len(e) else np.zeros(1))
+
+
+def objective(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None, z_edges=None, maps=None):
+    """J of adjoint_gradient alone (for finite differences); maps (with
+    z_edges) is a map that changes along z, as in propagate_map_z."""
     a = _stack(fields)
     dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
     w = np.ascontiguousarray(weights, dtype=np.float64)
     ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    if maps is not None:
+        mz, e = _zmaps(prob, z_edges, maps)
+        return float(_load().orc_objective_z(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
+                                             _dptr(ph), int(phi_field), _dptr(w), int(len(mz)), _dptr(e), _dptr(mz)))
     m = _map(prob, dk_map)
     return float(_load().orc_objective(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
                                        _dptr(ph), int(phi_field), _dptr(w), _dptr(m)))
 
 
-def adjoint_gradient(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None):
+def adjoint_gradient(prob, fields, nz, dz, dk, weights, phi=None, phi_field=1, dk_map=None, z_edges=None, maps=None):
     """J = sum_f w_f sum |A_f(L)|^2 and its gradient with respect to the
     spectral phase phi (centred order, applied to field phi_field) and the
     per-step mismatch, optionally under a transverse mismatch map dk_map
-    [ny, nx].  Returns (J, grad_phi or None, grad_dk)."""
+    [ny, nx] or a map that changes along z (maps [nseg, ny, nx] with
+    z_edges, as in propagate_map_z).  Returns (J, grad_phi or None, grad_dk)."""
     a = _stack(fields)
     dks = np.ascontiguousarray(np.broadcast_to(np.asarray(dk, dtype=np.float64), (nz,)))
     w = np.ascontiguousarray(weights, dtype=np.float64)
     ph = None if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
     gphi = None if phi is None else np.zeros(prob.nt)
     gdk = np.zeros(nz)
+    if maps is not None:
+        mz, e = _zmaps(prob, z_edges, maps)
+        J = _load().orc_adjoint_gradient_z(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
+                                           _dptr(ph), int(phi_field), _dptr(w), _dptr(gphi), _dptr(gdk),
+                                           int(len(mz)), _dptr(e), _dptr(mz))
+        return float(J), gphi, gdk
     m = _map(prob, dk_map)
     J = _load().orc_adjoint_gradient(ctypes.byref(prob), a.ctypes.data, int(nz), float(dz), _dptr(dks),
                                      _dptr(ph), int(phi_field), _dptr(w), _dptr(gphi), _dptr(gdk), _dptr(m))

@@ -489,6 +489,26 @@ int orc_propagate_map(const orc_problem* pb, cplx* fields, int nz, double dz, co
   return 0;
 }
 
+/* Segment of step j: the one that holds the step's midpoint (j + 1/2) dz. */
+static int segment_of_step(int j, double dz, int nseg, const double* z_edges) {
+  const double zmid = (j + 0.5) * dz;
+  int s = 0;
+  while (s < nseg - 1 && z_edges[s] <= zmid) ++s;
+  return s;
+}
+
+/* One split step under the map m with the per-point phase offset q at its
+ * start; q is advanced by m dz (qh: scratch for the second half step). */
+static void step_map_z(const orc_problem* pb, cplx* fields, double ph, double dk, double dz, double* q,
+                       const double* m, double* qh) {
+  const int64_t plane = (int64_t)pb->nx * pb->ny;
+  nonlinear_step_q(pb, fields, ph, dk, 0.5 * dz, q, m);
+  orc_linear_step(pb, fields, dz);
+  for (int64_t i = 0; i < plane; ++i) qh[i] = q[i] + m[i] * (0.5 * dz);
+  nonlinear_step_q(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz, qh, m);
+  for (int64_t i = 0; i < plane; ++i) q[i] += m[i] * dz;
+}
+
 /* A mismatch map that changes along z (a z-resolved thermal load, say):
  * Delta k(x, y, z) = dk_steps[j] + maps[s][y nx + x] on step j, s the segment
  * that holds the step's midpoint z_j + dz/2, segments separated by the
@@ -509,16 +529,9 @@ int orc_propagate_map_z(const orc_problem* pb, cplx* fields, int nz, double dz, 
   }
   double ph = *phi;
   for (int j = 0; j < nz; ++j) {
-    const double dk = dk_steps[j], zmid = (j + 0.5) * dz;
-    int s = 0;
-    while (s < nseg - 1 && z_edges[s] <= zmid) ++s;
-    const double* m = maps + (int64_t)s * plane;
-    nonlinear_step_q(pb, fields, ph, dk, 0.5 * dz, q, m);
-    orc_linear_step(pb, fields, dz);
-    for (int64_t i = 0; i < plane; ++i) qh[i] = q[i] + m[i] * (0.5 * dz);
-    nonlinear_step_q(pb, fields, ph + dk * 0.5 * dz, dk, 0.5 * dz, qh, m);
-    for (int64_t i = 0; i < plane; ++i) q[i] += m[i] * dz;
-    ph += dk * dz;
+    const double* m = maps + (int64_t)segment_of_step(j, dz, nseg, z_edges) * plane;
+    step_map_z(pb, fields, ph, dk_steps[j], dz, q, m, qh);
+    ph += dk_steps[j] * dz;
   }
   free(q);
   free(qh);
@@ -795,6 +808,7 @@ typedef struct {
   double phi_a, dk, h;
   double z_a;            /* distance of the half step's start from z = 0 (for the map) */
   const double* dk_map;  /* transverse mismatch map [ny][nx] or NULL */
+  const double* q;       /* per-point phase offset at the start [ny][nx] (replaces dk_map z_a) or NULL */
   double* part;  /* [slot][3] partial stage sensitivities */
   int64_t chunk; /* points per slot (fixed, so the sums do not depend on threads) */
 } vjp_job;
@@ -814,9 +828,10 @@ static void vjp_slots(void* p, int64_t s0, int64_t s1) {
         x[f] = j->x[f * n + i];
         gy[f] = j->g[f * n + i];
       }
-      /* with a map the point's phase is Phi_a + m z_a at the start and grows at dk + m */
+      /* with a map the point's phase is Phi_a + m z_a (or Phi_a + q) at the start and grows at dk + m */
       const double m = j->dk_map ? j->dk_map[i % plane] : 0.0;
-      orc_rk4_vjp_point(nf, j->kap, j->phi_a + m * j->z_a, j->dk + m, j->h, x, gy, gx, acc);
+      const double start = j->q ? j->phi_a + j->q[i % plane] : j->phi_a + m * j->z_a;
+      orc_rk4_vjp_point(nf, j->kap, start, j->dk + m, j->h, x, gy, gx, acc);
       for (int f = 0; f < nf; ++f) j->g[f * n + i] = gx[f];
     }
     for (int k = 0; k < 3; ++k) j->part[s * 3 + k] = acc[k];
@@ -843,6 +858,35 @@ void orc_nonlinear_step_adjoint_map(const orc_problem* pb, const cplx* x, cplx* 
   j.h = h;
   j.z_a = z_a;
   j.dk_map = dk_map;
+  j.q = NULL;
+  j.part = part;
+  j.chunk = chunk;
+  parallel_for(slots, vjp_slots, &j);
+  sens[0] = sens[1] = sens[2] = 0.0;
+  for (int64_t s = 0; s < slots; ++s)
+    for (int k = 0; k < 3; ++k) sens[k] += part[s * 3 + k];
+  free(part);
+}
+
+/* The same with a per-point phase offset: Phi(x, y, z_a + s) = phi_a + q(x, y)
+ * + (dk + dk_map(x, y)) s (a map that changes along z). */
+static void nonlinear_step_adjoint_q(const orc_problem* pb, const cplx* x, cplx* g, double phi_a, double dk,
+                                     double h, const double* q, const double* dk_map, double* sens) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  const int64_t chunk = 4096;
+  int64_t slots = (n + chunk - 1) / chunk;
+  double* part = (double*)calloc(3 * (size_t)slots, sizeof(double));
+  vjp_job j;
+  j.pb = pb;
+  j.x = x;
+  j.g = g;
+  for (int f = 0; f < pb->nf; ++f) j.kap[f] = orc_kappa(pb, f);
+  j.phi_a = phi_a;
+  j.dk = dk;
+  j.h = h;
+  j.z_a = 0.0;
+  j.dk_map = dk_map;
+  j.q = q;
   j.part = part;
   j.chunk = chunk;
   parallel_for(slots, vjp_slots, &j);
@@ -863,24 +907,37 @@ void orc_nonlinear_step_adjoint(const orc_problem* pb, const cplx* x, cplx* g, d
  * transverse map dk_map (NULL for none; the map itself is not a parameter).
  * Forward states of every step are kept (the oracle is for small grids).
  * Returns J. */
-double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
-                            const double* phi, int phi_field, const double* w, double* grad_phi,
-                            double* grad_dk, const double* dk_map) {
+/* Under a map that changes along z (maps non-NULL: nseg segments, as in
+ * orc_propagate_map_z) each step j keeps its per-point phase offset q_j, the
+ * integral of the maps up to z_j, and both half steps and their adjoints run
+ * with the map of the step's segment. */
+static double adjoint_impl(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                           const double* phi, int phi_field, const double* w, double* grad_phi, double* grad_dk,
+                           const double* dk_map, int nseg, const double* z_edges, const double* maps) {
   int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  const int64_t plane = (int64_t)pb->nx * pb->ny;
   int nf = pb->nf;
   int64_t sz = n * nf;
   cplx* st = (cplx*)malloc(sizeof(cplx) * sz * (size_t)(nz + 1)); /* A_0 .. A_nz */
   memcpy(st, fields_in, sizeof(cplx) * sz);
   if (phi) orc_spectral_phase(pb, st + phi_field * n, phi, +1);
   double* phis = (double*)malloc(sizeof(double) * (nz + 1)); /* Phi(z_j) */
+  double* qs = maps ? (double*)calloc((size_t)plane * (nz + 1), sizeof(double)) : NULL; /* q_j */
+  double* qh = maps ? (double*)malloc(sizeof(double) * (size_t)plane) : NULL;
   phis[0] = 0.0;
   for (int j = 0; j < nz; ++j) {
     memcpy(st + (j + 1) * sz, st + j * sz, sizeof(cplx) * sz);
     double ph = phis[j];
-    if (dk_map)
+    if (maps) {
+      const double* m = maps + (int64_t)segment_of_step(j, dz, nseg, z_edges) * plane;
+      memcpy(qs + (j + 1) * plane, qs + j * plane, sizeof(double) * plane);
+      step_map_z(pb, st + (j + 1) * sz, ph, dk_steps[j], dz, qs + (j + 1) * plane, m, qh);
+      ph += dk_steps[j] * dz;
+    } else if (dk_map) {
       orc_propagate_map(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph, j * dz, dk_map);
-    else
+    } else {
       orc_propagate(pb, st + (j + 1) * sz, 1, dz, dk_steps + j, &ph);
+    }
     phis[j + 1] = ph;
   }
   /* objective and its gradient at z = L */
@@ -902,6 +959,17 @@ double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz
     const double zj = j * dz;
     /* a2 = L(N_A(A_j)) */
     memcpy(a2, aj, sizeof(cplx) * sz);
+    if (maps) {
+      const double* m = maps + (int64_t)segment_of_step(j, dz, nseg, z_edges) * plane;
+      const double* q = qs + j * plane;
+      nonlinear_step_q(pb, a2, phis[j], dk, 0.5 * dz, q, m);
+      orc_linear_step(pb, a2, dz);
+      for (int64_t i = 0; i < plane; ++i) qh[i] = q[i] + m[i] * (0.5 * dz);
+      nonlinear_step_adjoint_q(pb, a2, g, phis[j] + dk * 0.5 * dz, dk, 0.5 * dz, qh, m, S + j * 6 + 3);
+      orc_linear_step_adjoint(pb, g, dz);
+      nonlinear_step_adjoint_q(pb, aj, g, phis[j], dk, 0.5 * dz, q, m, S + j * 6);
+      continue;
+    }
     if (dk_map)
       orc_nonlinear_step_map(pb, a2, phis[j], dk, 0.5 * dz, zj, dk_map);
     else
@@ -955,8 +1023,24 @@ double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz
   free(S);
   free(g);
   free(phis);
+  free(qs);
+  free(qh);
   free(st);
   return J;
+}
+
+double orc_adjoint_gradient(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                            const double* phi, int phi_field, const double* w, double* grad_phi,
+                            double* grad_dk, const double* dk_map) {
+  return adjoint_impl(pb, fields_in, nz, dz, dk_steps, phi, phi_field, w, grad_phi, grad_dk, dk_map, 0, NULL, NULL);
+}
+
+/* orc_adjoint_gradient under a map that changes along z (orc_propagate_map_z). */
+double orc_adjoint_gradient_z(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                              const double* phi, int phi_field, const double* w, double* grad_phi, double* grad_dk,
+                              int nseg, const double* z_edges, const double* maps) {
+  return adjoint_impl(pb, fields_in, nz, dz, dk_steps, phi, phi_field, w, grad_phi, grad_dk, NULL, nseg, z_edges,
+                      maps);
 }
 
 /* J only (for finite differences): the same forward map as above. */
@@ -972,6 +1056,24 @@ double orc_objective(const orc_problem* pb, const cplx* fields_in, int nz, doubl
     orc_propagate_map(pb, a, nz, dz, dk_steps, &ph, 0.0, dk_map);
   else
     orc_propagate(pb, a, nz, dz, dk_steps, &ph);
+  double J = 0.0;
+  for (int f = 0; f < nf; ++f)
+    for (int64_t i = 0; i < n; ++i) J += w[f] * (creal(a[f * n + i]) * creal(a[f * n + i]) + cimag(a[f * n + i]) * cimag(a[f * n + i]));
+  free(a);
+  return J;
+}
+
+/* J only, under a map that changes along z. */
+double orc_objective_z(const orc_problem* pb, const cplx* fields_in, int nz, double dz, const double* dk_steps,
+                       const double* phi, int phi_field, const double* w, int nseg, const double* z_edges,
+                       const double* maps) {
+  int64_t n = (int64_t)pb->nx * pb->ny * pb->nt;
+  int nf = pb->nf;
+  cplx* a = (cplx*)malloc(sizeof(cplx) * n * nf);
+  memcpy(a, fields_in, sizeof(cplx) * n * nf);
+  if (phi) orc_spectral_phase(pb, a + phi_field * n, phi, +1);
+  double ph = 0.0;
+  orc_propagate_map_z(pb, a, nz, dz, dk_steps, &ph, nseg, z_edges, maps);
   double J = 0.0;
   for (int f = 0; f < nf; ++f)
     for (int64_t i = 0; i < n; ++i) J += w[f] * (creal(a[f * n + i]) * creal(a[f * n + i]) + cimag(a[f * n + i]) * cimag(a[f * n + i]));

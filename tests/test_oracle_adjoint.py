@@ -184,6 +184,72 @@ def test_gradient_under_mismatch_map_matches_differences(three):
     assert np.linalg.norm(gdk - gdk0) > 0.1 * np.linalg.norm(gdk)
 
 
+@pytest.mark.parametrize("three", [False, True])
+def test_gradient_under_map_changing_along_z(three):
+    """A map that changes along z (three segments).  Pins: maps uniform on
+    each segment give the gradient of the per-step profile with each step's
+    segment value added (1e-12); three segments holding one map give the
+    static-map gradient (1e-12); with three different maps the gradient
+    matches central differences of the z-resolved objective."""
+    rng = np.random.default_rng(53 + three)
+    if three:
+        g = wl.Grid(8, 8, 16, 6 * UM, 6 * UM, 30 * FS)
+        f = _fields3()
+        x, y, t = g.axes()
+        env = np.exp(-(x[None, None] ** 2 + y[None, :, None] ** 2) / (15 * UM) ** 2 - (t[:, None, None] / (120 * FS)) ** 2)
+        ins = [8e7 * env + 0j, 2e7 * env * np.exp(0.3j), 1e6 * (rng.standard_normal(env.shape) + 0j)]
+        nz, dz, w, pf = 12, 30 * UM, np.array([0.0, 1.0, 0.5]), 0
+        dk = rng.normal(300.0, 200.0, nz)
+    else:
+        g, f, ins = _small_shg()
+        x, y, _ = g.axes()
+        nz, dz, pf = 16, 40 * UM, 1
+        wF = np.sum(np.abs(ins[1]) ** 2)
+        w = np.array([f[0].n / (f[1].n * wF), 0.0])
+        dk = rng.normal(0, 0.1, nz) / MM
+    prob = oracle.make_problem(g, f, wl.D_EFF)
+    edges = [3.3 * dz, 8.6 * dz]
+    seg = np.searchsorted(edges, (np.arange(nz) + 0.5) * dz, side="right")
+    phi = rng.normal(0, 0.2, g.nt)
+    # uniform segments == step profile
+    vals = np.array([900.0, -1500.0, 600.0])
+    uni = np.stack([np.full((g.ny, g.nx), v) for v in vals])
+    Ju, gphu, gdku = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf, z_edges=edges, maps=uni)
+    Jp, gphp, gdkp = oracle.adjoint_gradient(prob, ins, nz, dz, dk + vals[seg], w, phi=phi, phi_field=pf)
+    assert Ju == pytest.approx(Jp, rel=1e-12)
+    assert np.linalg.norm(gdku - gdkp) <= 1e-12 * np.linalg.norm(gdkp)
+    assert np.linalg.norm(gphu - gphp) <= 1e-12 * np.linalg.norm(gphp)
+    # one map on every segment == the static map
+    m = 4e6 * x[None, :] + 3e3 * np.exp(-(x[None, :] ** 2 + y[:, None] ** 2) / (12 * UM) ** 2) + 0 * y[:, None]
+    Js, gphs, gdks = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf, dk_map=m)
+    J3, gph3, gdk3 = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf, z_edges=edges,
+                                             maps=np.stack([m, m, m]))
+    assert J3 == pytest.approx(Js, rel=1e-12)
+    assert np.linalg.norm(gdk3 - gdks) <= 1e-12 * np.linalg.norm(gdks)
+    assert np.linalg.norm(gph3 - gphs) <= 1e-12 * np.linalg.norm(gphs)
+    # three different maps against central differences
+    maps = np.stack([m, 2000.0 - 0.7 * m, 0.5 * m - 800.0])
+    J, gphi, gdk = oracle.adjoint_gradient(prob, ins, nz, dz, dk, w, phi=phi, phi_field=pf, z_edges=edges, maps=maps)
+    assert J == pytest.approx(oracle.objective(prob, ins, nz, dz, dk, w, phi, pf, z_edges=edges, maps=maps), rel=1e-14)
+    hk = 1.0
+    for j in (0, 3, 4, nz - 1):  # around the first edge and at the ends
+        e = np.zeros(nz)
+        e[j] = hk
+        fd = (oracle.objective(prob, ins, nz, dz, dk + e, w, phi, pf, z_edges=edges, maps=maps) -
+              oracle.objective(prob, ins, nz, dz, dk - e, w, phi, pf, z_edges=edges, maps=maps)) / (2 * hk)
+        assert abs(gdk[j] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (j, gdk[j], fd)
+    def fd_phi(p, h):
+        e = np.zeros(g.nt)
+        e[p] = h
+        return (oracle.objective(prob, ins, nz, dz, dk, w, phi + e, pf, z_edges=edges, maps=maps) -
+                oracle.objective(prob, ins, nz, dz, dk, w, phi - e, pf, z_edges=edges, maps=maps)) / (2 * h)
+
+    for p in (0, g.nt // 2, g.nt - 1):  # the zero-frequency bin has the largest curvature: Richardson over h, h/2
+        fd = (4 * fd_phi(p, 5e-4) - fd_phi(p, 1e-3)) / 3
+        assert abs(gphi[p] - fd) <= 1e-6 * abs(fd) + 1e-9 * abs(J), (p, gphi[p], fd)
+    assert np.linalg.norm(gdk - gdks) > 0.05 * np.linalg.norm(gdk)
+
+
 def _centred_omega(nt, dt):
     """Omega_p = 2 pi (p - NT/2) / (NT dt): the centred order of the spectral-phase vector."""
     return 2 * np.pi * (np.arange(nt) - nt // 2) / (nt * dt)
