@@ -140,8 +140,7 @@ brahms_status brahms_set_dk_map(brahms_ctx* ctx, const double* dk_map);
  * (below); a change of segments drops the loads accumulated so far.  nseg == 1
  * is brahms_set_dk_map.  E_ARG for nseg outside 1..4096, bad edges or
  * non-finite maps; E_OOM if the segment maps (2 nseg ny nx doubles) cannot be
- * allocated.  The adjoint refuses a context with more than one segment
- * (E_STATE). */
+ * allocated.  The adjoint takes up to 16 segments (E_STATE beyond). */
 brahms_status brahms_set_dk_map_z(brahms_ctx* ctx, int nseg, const double* z_edges, const double* maps);
 
 /* Diagnostics of the current fields (the Sec. 6 power formula resolved in
@@ -273,13 +272,19 @@ long long brahms_launch_count(const brahms_ctx* ctx);
  * allocates (ceil(nz/K) + 2K + 2) field states plus small tables for it.
  * checkpoint_interval < 0: the forward records all 2 nz such states itself
  * (2 nz + 3 field states; on a large-memory GPU usually affordable) and the
- * backward recomputes nothing.  The gradient is bit-identical either way.
+ * backward recomputes nothing.  The gradient is bit-identical either way
+ * under a map constant in z.  Under a map that changes along z
+ * (brahms_set_dk_map_z, up to 16 segments) the recomputation and the reverse
+ * sweep form each step's map phase from the segments' step counts, which
+ * agrees with the forward's running sum to rounding, so the checkpointed and
+ * the recorded forms then agree to rounding.
  * ---------------------------------------------------------------------- */
 
 /* Set the fields (as brahms_set_fields), apply the phase (phi may be NULL),
  * propagate nz steps of dz with the profile dk, keep checkpoints, and return
  * J (weights: nfields entries).  Leaves the fields at z = nz dz.  Waits.
- * E_SIZE on grids with ny = 1 or nt = 1. */
+ * E_SIZE on grids with ny = 1 or nt = 1; E_STATE under a map of more than 16
+ * z-segments. */
 brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields, int dtype, int on_device,
                                      const double* phi, int phi_field, const double* dk, int nz, double dz,
                                      const double* weights, int checkpoint_interval, double* J);

@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "ctx_internal.h"
+#include "map_seg.h"
 
 using namespace brahms_host;
 
@@ -37,6 +38,37 @@ brahms_status linear_yty(brahms_ctx* ctx, float2* data, bool adjoint) {
   return BRAHMS_OK;
 }
 
+// Stage factors of the x-pass that applies the B half of step jB and the A
+// half of step jA (distances from z = 0).  One map: the running-sum tables of
+// the forward.  A map that changes along z: the closed form from the steps'
+// z-segments recorded by brahms_adjoint_forward (adj_zseg, and adj_zcnt, the
+// steps of every z-segment before each step).
+brahms_status adj_map_tables(brahms_ctx* ctx, int jB, int jA, double phiB, double dkB, double phiA, double dkA,
+                             double dz) {
+  if (!ctx->have_map) return BRAHMS_OK;
+  if (ctx->nseg == 1) return enqueue_map_tables(ctx, phiB, dkB, jB * dz, phiA, dkA, jA * dz, dz);
+  const int nz = ctx->adj_nz, nseg = ctx->nseg;
+  const int b = std::min(std::max(jB, 0), nz), a = std::min(std::max(jA, 0), nz);
+  brahms::MapSegArgs m{};
+  m.maps = ctx->maps_dev;
+  m.emap = ctx->emap_dev;
+  m.nxy = (long long)ctx->nx * ctx->ny;
+  m.nseg = nseg;
+  m.sB = ctx->adj_zseg[std::min(b, nz - 1)];
+  m.sA = ctx->adj_zseg[std::min(a, nz - 1)];
+  for (int s = 0; s < nseg; ++s) {
+    m.cB[s] = dz * ctx->adj_zcnt[(size_t)b * nseg + s];
+    m.cA[s] = dz * ctx->adj_zcnt[(size_t)a * nseg + s];
+  }
+  m.phiB = phiB;
+  m.dkB = dkB;
+  m.phiA = phiA;
+  m.dkA = dkA;
+  m.dz = dz;
+  BR_CK(launch(ctx, 4, 1, [&] { return brahms::run_map_tables_seg(m, ctx->stream); }));
+  return BRAHMS_OK;
+}
+
 // Steps j0 .. j1-1 from the real-space state in data (the state entering
 // step j0's A half step) in the forward's pass structure, with the recording
 // x-pass: a2_j (entering step j's B half step) goes to recB[j - j0] and A_j
@@ -51,7 +83,7 @@ brahms_status record_steps(brahms_ctx* ctx, float2* data, int j0, int j1, double
     x.data = data;
     x.phiA = ctx->adj_phis[j0];
     x.dkA = dk_at(j0);
-    brahms_status sm = enqueue_map_tables(ctx, 0.0, 0.0, j0 * dz, x.phiA, x.dkA, j0 * dz, dz);
+    brahms_status sm = adj_map_tables(ctx, j0, j0, 0.0, 0.0, x.phiA, x.dkA, dz);
     if (sm != BRAHMS_OK) return sm;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass(nx, nf, x, ctx->stream); }));
   }
@@ -67,7 +99,7 @@ brahms_status record_steps(brahms_ctx* ctx, float2* data, int j0, int j1, double
     x.dkA = dk_at(j + 1);
     x.rec_b = recB + (size_t)(j - j0) * nf * n;
     x.rec_a = last ? nullptr : recA + (size_t)(j + 1 - j0) * nf * n;
-    s2 = enqueue_map_tables(ctx, x.phiB, x.dkB, j * dz, x.phiA, x.dkA, (j + 1) * dz, dz);
+    s2 = adj_map_tables(ctx, j, j + 1, x.phiB, x.dkB, x.phiA, x.dkA, dz);
     if (s2 != BRAHMS_OK) return s2;
     BR_CK(launch(ctx, 0, 1, [&] { return brahms::run_xpass_record(nx, nf, x, ctx->stream); }));
   }
@@ -124,7 +156,8 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
   // any failure below leaves no forward for brahms_adjoint_backward to reverse
   ctx->adj_ready = false;
   if (ctx->ny < 2 || ctx->nt < 2) return fail(ctx, BRAHMS_E_SIZE, "the adjoint needs ny >= 2 and nt >= 2");
-  if (ctx->nseg > 1) return fail(ctx, BRAHMS_E_STATE, "the adjoint takes a mismatch map constant in z");
+  if (ctx->nseg > brahms::kMapSegMax)
+    return fail(ctx, BRAHMS_E_STATE, "the adjoint takes a mismatch map of at most 16 z-segments");
   if (!dk || !weights || nz < 1 || !(dz > 0) || !std::isfinite(dz))
     return fail(ctx, BRAHMS_E_ARG, "need dk[nz], weights[nfields], nz >= 1, dz > 0");
   if (phi && (phi_field < 0 || phi_field >= ctx->nf)) return fail(ctx, BRAHMS_E_ARG, "phi_field out of range");
@@ -181,6 +214,22 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
   }
   ctx->adj_phis[nz] = ph;
   ctx->adj_store_all = store_all;
+  if (ctx->nseg > 1) {
+    // the z-segment of every step, as brahms_propagate picks it from the
+    // distances it accumulates (one call of nz steps, or one per checkpoint)
+    const int zs = ctx->nseg;
+    ctx->adj_zseg.assign(nz, 0);
+    ctx->adj_zcnt.assign((size_t)(nz + 1) * zs, 0);
+    double zc = 0.0;
+    for (int j0 = 0; j0 < nz; j0 += store_all ? nz : K) {
+      const int cnt = std::min(store_all ? nz : K, nz - j0);
+      for (int i = 0; i < cnt; ++i) ctx->adj_zseg[j0 + i] = seg_of(ctx, (i == 0 ? zc : zc + i * dz) + 0.5 * dz);
+      zc += cnt * dz;
+    }
+    for (int j = 0; j < nz; ++j)
+      for (int q = 0; q < zs; ++q)
+        ctx->adj_zcnt[(size_t)(j + 1) * zs + q] = ctx->adj_zcnt[(size_t)j * zs + q] + (ctx->adj_zseg[j] == q);
+  }
   if (store_all) {
     // the forward records every step's B and A inputs; A_0 is the checkpoint
     BR_CK(cudaMemcpyAsync(ctx->adj_ckpt, ctx->state, sizeof(float2) * ctx->nf * n, cudaMemcpyDeviceToDevice,
@@ -192,6 +241,20 @@ brahms_status brahms_adjoint_forward(brahms_ctx* ctx, const void* const* fields,
     ctx->phi = ph;
     ctx->step += nz;
     ctx->z += nz * dz;
+    if (ctx->nseg > 1 && ctx->have_map) {
+      // the map's share of the phase at z = L, for a propagation that goes on from here
+      for (int q = 0; q < ctx->nseg; ++q) {
+        const double len = dz * ctx->adj_zcnt[(size_t)nz * ctx->nseg + q];
+        const double* mq = ctx->maps_dev + (size_t)q * ctx->nx * ctx->ny;
+        if (len != 0.0)
+          BR_CK(launch(ctx, 4, 1, [&] {
+            return brahms::run_map_phase_advance(ctx->mphase_dev, mq, len, (long long)ctx->nx * ctx->ny, ctx->stream);
+          }));
+      }
+      ctx->mphase_live = true;
+      ctx->map_zp = ctx->z;
+      ctx->map_cur = -1;
+    }
   } else {
     for (int seg = 0; seg < nseg; ++seg) {
       BR_CK(cudaMemcpyAsync(ctx->adj_ckpt + (size_t)seg * ctx->nf * n, ctx->state, sizeof(float2) * ctx->nf * n,
@@ -258,8 +321,8 @@ brahms_status brahms_adjoint_backward(brahms_ctx* ctx, double gscale, double* gr
     if (ctx->have_map) {
       // stage factors of step b-1's B half and step b's A half (distances from z = 0)
       r.emap = ctx->emap_dev;
-      const brahms_status sm = enqueue_map_tables(ctx, b > 0 ? ctx->adj_phis[b - 1] : 0.0, b > 0 ? dk_at(b - 1) : 0.0,
-                                                  (b - 1) * dz, ctx->adj_phis[b], dk_at(b), b * dz, dz);
+      const brahms_status sm = adj_map_tables(ctx, b - 1, b, b > 0 ? ctx->adj_phis[b - 1] : 0.0,
+                                              b > 0 ? dk_at(b - 1) : 0.0, ctx->adj_phis[b], dk_at(b), dz);
       if (sm != BRAHMS_OK) return sm;
     }
     long long ncta = 0;

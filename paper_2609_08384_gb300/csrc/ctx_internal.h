@@ -144,6 +144,7 @@ struct brahms_ctx {
   unsigned long long adj_gen = 0;  // gen at the end of the last brahms_adjoint_forward
   bool adj_store_all = false;  // the forward recorded every step (no recomputation)
   std::vector<double> adj_weights, adj_dk, adj_phis;
+  std::vector<int> adj_zseg, adj_zcnt;  // z-segment of every step; steps per z-segment before every step
   // thermal model (allocated on first use)
   char* th_mem = nullptr;
   int th_nseg = 0;             // segments th_mem holds

@@ -1,5 +1,6 @@
 // Set-up tables, the energy reduction and dtype conversions.
 #include "kernels.cuh"
+#include "map_seg.h"
 
 namespace brahms {
 
@@ -95,6 +96,33 @@ cudaError_t run_map_phase_advance(double* mphase, const double* m, double len, l
   long long g = (nxy + 255) / 256;
   if (g > 152 * 8) g = 152 * 8;
   map_phase_advance_kernel<<<(unsigned)g, 256, 0, s>>>(mphase, m, len, nxy);
+  return cudaPeekAtLastError();
+}
+
+// B: the second half of step jB (starting at its midpoint), A: the first half
+// of step jA; the same four tables as map_tables_kernel.
+__global__ void map_tables_seg_kernel(const MapSegArgs a) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.nxy;
+       i += (long long)gridDim.x * blockDim.x) {
+    double qb = 0.0, qa = 0.0;
+    for (int s = 0; s < a.nseg; ++s) {
+      const double m = a.maps[s * a.nxy + i];
+      qb += a.cB[s] * m;
+      qa += a.cA[s] * m;
+    }
+    const double mb = a.maps[a.sB * a.nxy + i], ma = a.maps[a.sA * a.nxy + i];
+    a.emap[i] = phase_plus(a.phiB + a.dkB * 0.5 * a.dz + qb + mb * (0.5 * a.dz));
+    a.emap[a.nxy + i] = phase_plus((a.dkB + mb) * 0.25 * a.dz);
+    a.emap[2 * a.nxy + i] = phase_plus(a.phiA + qa);
+    a.emap[3 * a.nxy + i] = phase_plus((a.dkA + ma) * 0.25 * a.dz);
+  }
+}
+
+cudaError_t run_map_tables_seg(const MapSegArgs& a, cudaStream_t s) {
+  if (a.nseg < 1 || a.nseg > kMapSegMax) return cudaErrorInvalidValue;
+  long long g = (a.nxy + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  map_tables_seg_kernel<<<(unsigned)g, 256, 0, s>>>(a);
   return cudaPeekAtLastError();
 }
 

@@ -36,11 +36,13 @@ def _shg_case(n, nt, nz, dz, seed, intensity=3e13):
     return g, f, ins, phi, dk
 
 
-def _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, phi_field=1, dk_map=None):
+def _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=0, phi_field=1, dk_map=None, z_edges=None, maps=None):
     import paper_2609_08384_gb300 as br
     s = br.Solver(g, f, wl.D_EFF, 0.0)
     if dk_map is not None:
         s.set_dk_map(dk_map)
+    if maps is not None:
+        s.set_dk_map_z(z_edges, maps)
     J = s.adjoint_forward([torch.from_numpy(a).cuda() for a in ins], dk, nz, dz, w, phi=phi, phi_field=phi_field,
                           checkpoint_interval=interval)
     gphi, gdk = s.adjoint_backward(1.0)
@@ -244,3 +246,49 @@ def test_store_all_forward_gives_the_same_gradient(with_map):
     got = _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=-1, dk_map=m)
     assert got[0] == ref[0]
     assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2])
+
+
+@pytest.mark.parametrize("three", [False, True])
+def test_gradient_under_map_changing_along_z_matches_oracle(three):
+    """Three z-segments with different maps: the adjoint's recomputation and
+    reverse sweep form each step's map phase from the segments' step counts;
+    the gradient matches the oracle's z-resolved gradient with the default
+    checkpoints, an interval of 7 steps and every step recorded."""
+    if three:
+        g = wl.Grid(24, 16, 32, 6 * wl.UM, 6 * wl.UM, 30 * wl.FS)
+        f = [wl.FieldParams(wl.LAM_P, wl.N_P, delta=1e-10, k2=2e-25, rho=2e-3),
+             wl.FieldParams(wl.LAM_S, wl.N_S, k2=1e-25),
+             wl.FieldParams(wl.LAM_I, wl.N_I, delta=-1e-10, k2=5e-26, rho=1e-3, alpha=20.0)]
+        x, y, t = g.axes()
+        env = np.exp(-(x[None, None] ** 2 + y[None, :, None] ** 2) / (25 * wl.UM) ** 2 - (t[:, None, None] / (150 * wl.FS)) ** 2)
+        rng = np.random.default_rng(19)
+        ins = [(8e7 * env).astype(np.complex64), (2e7 * env * np.exp(0.3j)).astype(np.complex64),
+               (1e6 * rng.standard_normal(env.shape)).astype(np.complex64)]
+        nz, dz, pf = 16, 25 * wl.UM, 0
+        dk = rng.normal(300.0, 200.0, nz)
+        phi = rng.normal(0, 0.2, g.nt)
+        w = np.array([0.0, 1e-15, 5e-16])
+        m = _fanout_map(g, slope=2e7, bump=2e4, width=15 * wl.UM)
+    else:
+        nz = 60
+        dz = 5 * wl.UM * (400 / nz) * 0.25
+        g, f, ins, phi, dk = _shg_case(32, 64, nz, dz, 89)
+        w = np.array([f[0].n / (f[1].n * float(np.sum(np.abs(ins[1].astype(np.complex128)) ** 2))), 0.0])
+        pf = 1
+        m = _fanout_map(g)
+    maps = np.stack([m, 0.5 * m.max() - 0.8 * m, 0.4 * m])
+    edges = [0.31 * nz * dz, 0.72 * nz * dz]
+    prob = oracle.make_problem(g, f, wl.D_EFF)
+    ins128 = [a.astype(np.complex128) for a in ins]
+    Jr, gphi_r, gdk_r = oracle.adjoint_gradient(prob, ins128, nz, dz, dk, w, phi=phi, phi_field=pf, z_edges=edges,
+                                                maps=maps)
+    errs = {}
+    for interval in (0, 7, -1):
+        J, gphi, gdk = _gpu_grad(g, f, ins, phi, dk, nz, dz, w, interval=interval, phi_field=pf, z_edges=edges,
+                                 maps=maps)
+        errs[interval] = (abs(J / Jr - 1), rel_l2(gphi, gphi_r), rel_l2(gdk, gdk_r))
+        assert errs[interval][0] < 1e-4, errs
+        assert errs[interval][1] < GRAD_TOL and errs[interval][2] < GRAD_TOL, errs
+    # the z-resolution is felt: the gradient under the first segment's map alone is far off
+    _, _, gdk1 = oracle.adjoint_gradient(prob, ins128, nz, dz, dk, w, phi=phi, phi_field=pf, dk_map=maps[0])
+    assert rel_l2(gdk1, gdk_r) > 20 * GRAD_TOL

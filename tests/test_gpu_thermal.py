@@ -249,11 +249,13 @@ def test_z_segment_status_codes():
     s.heat_set(np.ones((3, 8, 16)))
     t = s.thermal_map(1.0, 1.0)
     assert t.shape == (3, 8, 16) and (t > 0).all()
-    # the adjoint takes a map constant in z
+    # the adjoint takes up to 16 z-segments
+    s.adjoint_forward(_dev([z, z]), np.zeros(2), 2, 1e-5, np.array([1.0, 0.0]))
+    s.set_dk_map_z(1e-4 * np.arange(1, 17))
     with pytest.raises(br.BrahmsError) as ei:
         s.adjoint_forward(_dev([z, z]), np.zeros(2), 2, 1e-5, np.array([1.0, 0.0]))
     assert ei.value.status == br.BRAHMS_E_STATE
-    s.set_dk_map(None)  # back to one segment: the adjoint runs
+    s.set_dk_map(None)  # back to one segment
     s.adjoint_forward(_dev([z, z]), np.zeros(2), 2, 1e-5, np.array([1.0, 0.0]))
     s.close()
 
