@@ -367,6 +367,9 @@ brahms_status brahms_set_dk_map_z(brahms_ctx* ctx, int nseg, const double* z_edg
     ctx->nseg = 1;
     ctx->zedge.clear();
     ctx->have_user_map = ctx->have_therm = false;
+    // zero maps until the new ones are in (what stays in effect if the allocation fails)
+    BR_CK(cudaMemsetAsync(ctx->ws_map, 0, sizeof(double) * nxy, ctx->stream));
+    BR_CK(cudaMemsetAsync(ctx->ws_umap, 0, sizeof(double) * nxy, ctx->stream));
     if (nseg > 1) {
       const size_t plane = align256(sizeof(double) * nxy * nseg);
       if (brahms::dev_alloc((void**)&ctx->seg_mem, 2 * plane) != cudaSuccess) {
