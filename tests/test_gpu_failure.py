@@ -153,6 +153,20 @@ def test_allocation_failures_report_oom_and_leave_usable_state():
     sol.heat_set(np.ones((g.ny, g.nx)))
     sol.close()
 
+    # the planes of a map with z-segments: E_OOM, then zero maps in effect and a usable context
+    sol = br.Solver(g, fields, wl.D_EFF, 0.0)
+    zf = [torch.zeros(g.nt, g.ny, g.nx, dtype=torch.complex64).cuda() for _ in range(2)]
+    sol.set_fields(zf)
+    br.fail_next_allocations(1)
+    with pytest.raises(br.BrahmsError) as ei:
+        sol.set_dk_map_z([1e-4, 2e-4], np.ones((3, g.ny, g.nx)))
+    assert ei.value.status == br.BRAHMS_E_OOM
+    sol.propagate(2, 10 * wl.UM)
+    sol.set_dk_map_z([1e-4, 2e-4], np.ones((3, g.ny, g.nx)))
+    sol.propagate(2, 10 * wl.UM)
+    sol.sync()
+    sol.close()
+
     # a batch instance
     b = br.Batch()
     br.fail_next_allocations(1)
