@@ -91,17 +91,40 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
   if (act) {
     const long long nxy = (long long)p.ny * NX;
     const float2* emap = MAP ? p.emap + (row % p.ny) * NX : nullptr;
+    // the recorded states of the next point are requested while this one is
+    // reversed (measured on the adjoint workload: backward 152 -> 143 ms;
+    // requesting both states of the same point up front gained nothing)
+    float2 na[F], nb[F];
+    {
+      const long long at0 = row * NX + t;
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        na[f] = p.xa ? __ldcg(p.xa + f * p.fstride + at0) : make_float2(0.f, 0.f);
+        nb[f] = p.xb ? __ldcg(p.xb + f * p.fstride + at0) : make_float2(0.f, 0.f);
+      }
+    }
 #pragma unroll 1
     for (int e = 0; e < E; ++e) {
       const int pos = t + (e / RF0) * T + (e % RF0) * SF0;
       const int off = pos + (pos >> 4);
-      const long long at = row * NX + pos;
-      float2 g[F], x[F];
+      float2 g[F], x[F], xbv[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        x[f] = na[f];
+        xbv[f] = nb[f];
+      }
+      if (e + 1 < E) {
+        const int pn = t + ((e + 1) / RF0) * T + ((e + 1) % RF0) * SF0;
+        const long long an = row * NX + pn;
+#pragma unroll
+        for (int f = 0; f < F; ++f) {
+          if (p.xa) na[f] = __ldcg(p.xa + f * p.fstride + an);
+          if (p.xb) nb[f] = __ldcg(p.xb + f * p.fstride + an);
+        }
+      }
 #pragma unroll
       for (int f = 0; f < F; ++f) g[f] = myrow[f * ROWS * PITCH + off];
       if (p.xa) {
-#pragma unroll
-        for (int f = 0; f < F; ++f) x[f] = __ldcg(p.xa + f * p.fstride + at);
         if constexpr (MAP) {
           float2 c[3 * F];
           map_coef_sets<F>(__ldg(emap + 2 * nxy + pos), __ldg(emap + 3 * nxy + pos), p.kh, c);
@@ -112,7 +135,7 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
       }
       if (p.xb) {
 #pragma unroll
-        for (int f = 0; f < F; ++f) x[f] = __ldcg(p.xb + f * p.fstride + at);
+        for (int f = 0; f < F; ++f) x[f] = xbv[f];
         if constexpr (MAP) {
           float2 c[3 * F];
           map_coef_sets<F>(__ldg(emap + pos), __ldg(emap + nxy + pos), p.kh, c);
