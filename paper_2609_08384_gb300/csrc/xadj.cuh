@@ -91,10 +91,11 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
   if (act) {
     const long long nxy = (long long)p.ny * NX;
     const float2* emap = MAP ? p.emap + (row % p.ny) * NX : nullptr;
-    // the recorded states of the next point are requested while this one is
-    // reversed (measured on the adjoint workload: backward 152 -> 143 ms;
+    // the recorded states (and under a map the stage-factor tables) of the next
+    // point are requested while this one is reversed (measured on the adjoint
+    // workload: backward 152 -> 143 ms, under a fan-out map 168 -> 153 ms;
     // requesting both states of the same point up front gained nothing)
-    float2 na[F], nb[F];
+    float2 na[F], nb[F], nm[4];
     {
       const long long at0 = row * NX + t;
 #pragma unroll
@@ -102,16 +103,24 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
         na[f] = p.xa ? __ldcg(p.xa + f * p.fstride + at0) : make_float2(0.f, 0.f);
         nb[f] = p.xb ? __ldcg(p.xb + f * p.fstride + at0) : make_float2(0.f, 0.f);
       }
+      if constexpr (MAP) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) nm[q] = __ldg(emap + q * nxy + t);
+      }
     }
 #pragma unroll 1
     for (int e = 0; e < E; ++e) {
       const int pos = t + (e / RF0) * T + (e % RF0) * SF0;
       const int off = pos + (pos >> 4);
-      float2 g[F], x[F], xbv[F];
+      float2 g[F], x[F], xbv[F], cm[4];
 #pragma unroll
       for (int f = 0; f < F; ++f) {
         x[f] = na[f];
         xbv[f] = nb[f];
+      }
+      if constexpr (MAP) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cm[q] = nm[q];
       }
       if (e + 1 < E) {
         const int pn = t + ((e + 1) / RF0) * T + ((e + 1) % RF0) * SF0;
@@ -121,13 +130,17 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
           if (p.xa) na[f] = __ldcg(p.xa + f * p.fstride + an);
           if (p.xb) nb[f] = __ldcg(p.xb + f * p.fstride + an);
         }
+        if constexpr (MAP) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) nm[q] = __ldg(emap + q * nxy + pn);
+        }
       }
 #pragma unroll
       for (int f = 0; f < F; ++f) g[f] = myrow[f * ROWS * PITCH + off];
       if (p.xa) {
         if constexpr (MAP) {
           float2 c[3 * F];
-          map_coef_sets<F>(__ldg(emap + 2 * nxy + pos), __ldg(emap + 3 * nxy + pos), p.kh, c);
+          map_coef_sets<F>(cm[2], cm[3], p.kh, c);
           rk4_vjp_point<F>(x, g, c, sens[0], sens[1], sens[2]);
         } else {
           rk4_vjp_point<F>(x, g, cA, sens[0], sens[1], sens[2]);
@@ -138,7 +151,7 @@ __device__ __forceinline__ void xpass_adj_tile(const XAdjArgs& p, long long tile
         for (int f = 0; f < F; ++f) x[f] = xbv[f];
         if constexpr (MAP) {
           float2 c[3 * F];
-          map_coef_sets<F>(__ldg(emap + pos), __ldg(emap + nxy + pos), p.kh, c);
+          map_coef_sets<F>(cm[0], cm[1], p.kh, c);
           rk4_vjp_point<F>(x, g, c, sens[3], sens[4], sens[5]);
         } else {
           rk4_vjp_point<F>(x, g, cB, sens[3], sens[4], sens[5]);
